@@ -1,0 +1,170 @@
+/*
+ * pnce.h -- C ABI of libpnce, PN-sequence correlation channel estimation on GB300.
+ *
+ * What is computed (Sec. II, Eq. 2, 3 and 10 of "Channel Estimation for Massive MIMO
+ * systems using Tensor Cores in GPU"): K transmitters send cyclic shifts k*L of one
+ * length-N m-sequence pilot p; after cyclic-prefix removal every receive antenna
+ * correlates its N complex samples with every cyclic shift of p,
+ *
+ *     H[f][m][k][l] = (1/N) * sum_{n<N} Y[f][m][n] * p[(n - l - k*L) mod N],
+ *
+ * which is the circulant (Eq. 2) correlator (1/N) S^T Y of Eq. 3 / Eq. 10 restricted
+ * to the lags j = k*L + l < K*L.  p[n] = +1 for pilot bit 0 and -1 for bit 1.
+ *
+ * Conventions shared by every entry point
+ *  - Complex data are interleaved float32 pairs (re, im) ("complex64").
+ *    Y is [F][M][N] and H is [F][M][K][L] (equivalently [F*M][K*L], lag j = k*L + l),
+ *    both dense row-major.
+ *  - Pointers named *_dev are device pointers on the device that was current when the
+ *    handle was created; *_host are host pointers (page-locked memory recommended).
+ *    The caller owns Y, H, gradients and workspaces; the library owns only what its
+ *    own create functions return.  No estimate/backward call allocates memory.
+ *  - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls only enqueue work; results are ready when the stream reaches them.
+ *  - Every function returns a pnce_status and never aborts or prints.  Arguments are
+ *    validated before anything is launched; an invalid call launches nothing.
+ *    Errors raised on the device after launch (a bounded wait that ran out inside a
+ *    kernel) are latched in the handle and reported by pnce_get_status().
+ *  - Shape rules: F, M >= 1; N >= 2; K, L >= 1 and K*L <= N (Eq. 7 with C = L: the
+ *    cyclic shifts must not alias).  Device pointers must be 16-byte aligned.
+ */
+#ifndef PNCE_H
+#define PNCE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PNCE_OK = 0,
+    PNCE_EINVAL = 1,        /* bad argument: shape, null or misaligned pointer, small workspace */
+    PNCE_EUNSUPPORTED = 2,  /* valid request this build or device cannot serve */
+    PNCE_ENOMEM = 3,        /* a create function could not allocate */
+    PNCE_ECUDA = 4,         /* a CUDA runtime call failed */
+    PNCE_ETIMEOUT = 5,      /* a device-side bounded wait ran out (latched, see pnce_get_status) */
+    PNCE_ESTATE = 6         /* wrong device current, or handle/pilot mismatch */
+} pnce_status;
+
+/* Arithmetic of the correlation.  FP32_SIMT: exact FP32 on the CUDA cores.  The others
+ * quantise Y (per antenna, power-of-two scale) and run on the tensor cores with FP32
+ * accumulation; +-1 pilots are exact in every one of these formats. */
+typedef enum {
+    PNCE_FP32_SIMT = 0,
+    PNCE_TF32 = 1,
+    PNCE_FP16 = 2,
+    PNCE_BF16 = 3,
+    PNCE_FP8E4M3 = 4
+} pnce_dtype;
+
+typedef struct pnce_handle pnce_handle;   /* per-device context: latched device status */
+typedef struct pnce_pilot pnce_pilot;     /* device-resident pilot bit table of one sequence */
+
+/* Library version, major*10000 + minor*100 + patch. */
+int pnce_version(void);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* pnce_status_string(pnce_status s);
+
+/* Create a handle bound to the current device.  Allocates one small device status word. */
+pnce_status pnce_create(pnce_handle** out);
+pnce_status pnce_destroy(pnce_handle* h);
+
+/* Read (and clear) the status latched by kernels of this handle.  Synchronises stream. */
+pnce_status pnce_get_status(pnce_handle* h, void* stream);
+
+/*
+ * Pilot table (Sec. II-A: the m-sequence pilot, Eq. 1).  bits_host: ceil(N/32) uint32
+ * words, bit n of the sequence in word n/32 at bit n%32 (LSB first).  The library
+ * uploads a wrapped copy (bit t = bit (t mod N)) to device memory once; the call is
+ * synchronous.  N in [2, 2^24).
+ */
+pnce_status pnce_pilot_create(pnce_handle* h, const uint32_t* bits_host, int N, pnce_pilot** out);
+pnce_status pnce_pilot_destroy(pnce_pilot* p);
+
+/*
+ * Workspace bytes pnce_estimate needs for this shape and dtype (0 for FP32_SIMT).  The
+ * tensor-core dtypes keep the quantised operand there: 2*F*M rows (re, im per antenna)
+ * of ceil(N/64)*64 elements, plus per-antenna scales.  Returns 0 for invalid shapes.
+ */
+size_t pnce_workspace_size(int F, int M, int N, int K, int L, int dtype);
+
+/*
+ * Channel estimate, Eq. 3 / Eq. 10 (definition at the top of this file).
+ * Y_dev: complex64 [F][M][N]; H_dev: complex64 [F][M][K][L] (fully overwritten).
+ * dtype: a pnce_dtype.  For the tensor-core dtypes Y is first quantised per antenna
+ * (pnce_quantize) into workspace_dev, then correlated on the tensor cores; the FP32 SIMT
+ * path ignores the workspace (may be NULL).
+ */
+pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y_dev,
+                          int F, int M, int N, int K, int L, int dtype,
+                          void* workspace_dev, size_t workspace_bytes, void* H_dev,
+                          void* stream);
+
+/*
+ * Reduced-precision operand (Sec. III-B: conversion of the received block to the
+ * tensor-core input format).  For antenna a = f*M + m: A_a = max_n max(|Re y|, |Im y|)
+ * (exact in FP32), E_a = sum_n |y|^2 (FP64); scale 2^s_a with s_a = t - e where
+ * A_a = mant * 2^e, mant in [0.5, 1), t = 15 (fp16) or 8 (e4m3), s_a = 0 for bf16,
+ * tf32 and A_a = 0; s_a clamped to [-100, 100].  Writes, into workspace_dev, rows
+ * 2a (real part) and 2a+1 (imaginary part) of round(y * 2^s_a) in dtype (round to
+ * nearest even; e4m3 saturates at 448; tf32 rounds ties away), the per-antenna output
+ * factor 2^-s_a / N (float32) and, if power_dev != NULL, E_a / N (float64 [F*M]).
+ * exps_dev (int32 [F*M], may be NULL) receives s_a.  dtype must not be FP32_SIMT.
+ */
+pnce_status pnce_quantize(pnce_handle* h, const void* Y_dev, int F, int M, int N, int dtype,
+                          void* workspace_dev, size_t workspace_bytes, int32_t* exps_dev,
+                          double* power_dev, void* stream);
+
+/*
+ * Tensor-core correlation of an operand already quantised into workspace_dev by
+ * pnce_quantize (same F, M, N, dtype): the contraction and epilogue of pnce_estimate
+ * alone.  Lets callers time or overlap the quantisation separately.
+ */
+pnce_status pnce_correlate_quantized(pnce_handle* h, const pnce_pilot* pilot,
+                                     int F, int M, int N, int K, int L, int dtype,
+                                     const void* workspace_dev, size_t workspace_bytes,
+                                     void* H_dev, void* stream);
+
+/*
+ * Estimate with a real-valued pilot p_dev (float32 [N]) in place of the +-1 sequence:
+ * H = (1/N) sum_n Y[n] p[(n - j) mod N], FP32 on the CUDA cores.  This is the forward
+ * of the relaxed pilot p = tanh(theta) used for pilot optimisation.
+ */
+pnce_status pnce_estimate_real_pilot(pnce_handle* h, const float* p_dev, const void* Y_dev,
+                                     int F, int M, int N, int K, int L, void* H_dev,
+                                     void* stream);
+
+/*
+ * Adjoint of pnce_estimate_real_pilot for a real loss.  G_dev = dLoss/dRe(H) +
+ * i dLoss/dIm(H), complex64 [F][M][K][L].  Outputs (either may be NULL to skip):
+ *   dY_dev[f][m][n] = (1/N) sum_{j<KL} G[f][m][j] p[(n - j) mod N]      complex64
+ *   dp_dev[q]       = (1/N) sum_{f,m,j} Re(conj(G[f][m][j]) Y[f][m][(q + j) mod N])
+ * dp is reduced deterministically in two stages through workspace_dev
+ * (pnce_backward_workspace_size bytes).
+ */
+size_t pnce_backward_workspace_size(int F, int M, int N, int K, int L);
+pnce_status pnce_backward(pnce_handle* h, const float* p_dev, const void* Y_dev,
+                          const void* G_dev, int F, int M, int N, int K, int L,
+                          void* dY_dev, float* dp_dev, void* workspace_dev,
+                          size_t workspace_bytes, void* stream);
+
+/*
+ * End-to-end estimate from host memory: copies Y_host (complex64 [F][M][N]) to the
+ * device, estimates as pnce_estimate, and copies H back to H_host, all enqueued on
+ * stream.  The device buffers live in workspace_dev (pnce_host_workspace_size bytes).
+ * Frames are processed in chunks so that copies overlap the kernels.
+ */
+size_t pnce_host_workspace_size(int F, int M, int N, int K, int L, int dtype);
+pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const void* Y_host,
+                               int F, int M, int N, int K, int L, int dtype,
+                               void* workspace_dev, size_t workspace_bytes, void* H_host,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PNCE_H */

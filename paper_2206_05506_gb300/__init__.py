@@ -1,0 +1,292 @@
+"""PN-sequence correlation channel estimation on GB300 (sm_103a).
+
+Python face of libpnce (include/pnce.h).  PyTorch supplies device memory and streams;
+every step of the estimator runs in the library's CUDA kernels:
+
+    H[f, m, k, l] = (1/N) sum_n Y[f, m, n] p[(n - l - k L) mod N]
+
+(the correlator (1/N) S^T Y of Eq. 3 / Eq. 10 with K transmitters multiplexed by the
+cyclic shifts k*L of one m-sequence, Sec. II-B).
+
+    pilot = Pilot(bits)                       # 0/1 m-sequence bits, uploaded once
+    H = estimate(Y, pilot, K, L, dtype="fp16")  # Y: complex64 CUDA tensor [F, M, N]
+
+dtype: "fp32" (exact FP32 on the CUDA cores), or "tf32" / "fp16" / "bf16" / "e4m3"
+(per-antenna power-of-two scaled operand, tensor cores, FP32 accumulation).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import DTYPES, PnceError, check
+
+__all__ = ["Pilot", "Context", "estimate", "quantize", "correlate_quantized",
+           "estimate_real_pilot", "backward", "estimate_host", "workspace_size",
+           "host_workspace_size", "backward_workspace_size", "get_status", "DTYPES",
+           "PnceError", "lib"]
+
+
+def lib():
+    return _lib.load()
+
+
+def _dt(dtype) -> int:
+    if isinstance(dtype, int):
+        return dtype
+    try:
+        return DTYPES[dtype]
+    except KeyError:
+        raise ValueError(f"unknown dtype {dtype!r}; one of {sorted(DTYPES)}") from None
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _ptr(t) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+class Context:
+    """A pnce_handle bound to one CUDA device (latched device status word)."""
+
+    def __init__(self, device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().pnce_create(C.byref(h)), "pnce_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        return self._h
+
+    def status(self, stream=None) -> int:
+        with torch.cuda.device(self.device):
+            s = _stream(self.device) if stream is None else stream
+            return lib().pnce_get_status(self._h, s)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib._lib is not None:
+            _lib._lib.pnce_destroy(h)
+            self._h = None
+
+
+_ctx_lock = threading.Lock()
+_contexts: dict[int, Context] = {}
+
+
+def context(device=None) -> Context:
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    idx = dev.index if dev.index is not None else torch.cuda.current_device()
+    with _ctx_lock:
+        if idx not in _contexts:
+            _contexts[idx] = Context(idx)
+        return _contexts[idx]
+
+
+def get_status(device=None) -> int:
+    """Synchronise the current stream and return (and clear) the latched device status."""
+    return context(device).status()
+
+
+class Pilot:
+    """Device-resident m-sequence pilot (bits 0/1, bit 0 -> +1, bit 1 -> -1)."""
+
+    def __init__(self, bits, device=None):
+        b = np.asarray(bits.cpu().numpy() if isinstance(bits, torch.Tensor) else bits)
+        b = b.astype(np.uint8).ravel()
+        if b.size < 2 or np.any(b > 1):
+            raise ValueError("pilot bits must be a 0/1 array of length >= 2")
+        self.N = int(b.size)
+        nw = (self.N + 31) // 32
+        padded = np.zeros(nw * 32, dtype=np.uint64)
+        padded[: self.N] = b
+        words = (padded.reshape(nw, 32) << np.arange(32, dtype=np.uint64)).sum(axis=1)
+        self.words = np.ascontiguousarray(words.astype(np.uint32))
+        self.ctx = context(device)
+        self.device = self.ctx.device
+        p = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().pnce_pilot_create(self.ctx.handle,
+                                          self.words.ctypes.data_as(C.POINTER(C.c_uint32)),
+                                          self.N, C.byref(p)), "pnce_pilot_create")
+        self._p = p
+
+    @property
+    def handle(self):
+        return self._p
+
+    def __del__(self):
+        p = getattr(self, "_p", None)
+        if p is not None and _lib._lib is not None:
+            _lib._lib.pnce_pilot_destroy(p)
+            self._p = None
+
+
+def workspace_size(F, M, N, K, L, dtype) -> int:
+    return int(lib().pnce_workspace_size(F, M, N, K, L, _dt(dtype)))
+
+
+def backward_workspace_size(F, M, N, K, L) -> int:
+    return int(lib().pnce_backward_workspace_size(F, M, N, K, L))
+
+
+def host_workspace_size(F, M, N, K, L, dtype) -> int:
+    return int(lib().pnce_host_workspace_size(F, M, N, K, L, _dt(dtype)))
+
+
+_ws_cache: dict[tuple, torch.Tensor] = {}
+
+
+def _workspace(device, nbytes: int, key=None) -> torch.Tensor | None:
+    """A cached byte buffer per (device, stream, key), grown on demand."""
+    if nbytes == 0:
+        return None
+    k = (device.index, _stream(device), key)
+    buf = _ws_cache.get(k)
+    if buf is None or buf.numel() < nbytes:
+        buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        _ws_cache[k] = buf
+    return buf
+
+
+def _check_y(Y: torch.Tensor, pilot: Pilot | None = None):
+    if not isinstance(Y, torch.Tensor) or Y.dtype != torch.complex64 or Y.dim() != 3:
+        raise ValueError("Y must be a complex64 tensor [F, M, N]")
+    if not Y.is_cuda:
+        raise ValueError("Y must be a CUDA tensor (use estimate_host for host buffers)")
+    if not Y.is_contiguous():
+        raise ValueError("Y must be contiguous")
+    if pilot is not None and Y.shape[2] != pilot.N:
+        raise ValueError(f"Y has N={Y.shape[2]} samples but the pilot has N={pilot.N}")
+    return Y.shape
+
+
+def estimate(Y: torch.Tensor, pilot: Pilot, K: int, L: int, dtype="fp32", out=None,
+             workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """Channel estimate H [F, M, K, L] (complex64) of received blocks Y [F, M, N]."""
+    F, M, N = _check_y(Y, pilot)
+    dt = _dt(dtype)
+    dev = Y.device
+    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    need = workspace_size(F, M, N, K, L, dt)
+    ws = workspace if workspace is not None else _workspace(dev, need)
+    nbytes = 0 if ws is None else ws.numel() * ws.element_size()
+    with torch.cuda.device(dev):
+        check(lib().pnce_estimate(pilot.ctx.handle, pilot.handle, Y.data_ptr(), F, M, N, K, L,
+                                  dt, _ptr(ws), nbytes, H.data_ptr(), _stream(dev)),
+              "pnce_estimate")
+    return H
+
+
+def quantize(Y: torch.Tensor, dtype, workspace=None, want_power=False):
+    """Run only the quantisation step; returns a dict of views into the workspace.
+
+    'q': the operand as raw integer codes [F*M*2, pitch] (uint16 for fp16/bf16, int32 for
+    tf32, uint8 for e4m3), 'factor': float32 [F*M] = 2^-s / N, 'exps': int32 s,
+    'power': float64 mean power (if want_power), 'workspace': the buffer.
+    """
+    F, M, N = _check_y(Y)
+    dt = _dt(dtype)
+    if dt == 0:
+        raise ValueError("fp32 has no quantised operand")
+    dev = Y.device
+    need = workspace_size(F, M, N, 1, 1, dt)
+    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    exps = torch.empty(F * M, dtype=torch.int32, device=dev)
+    power = torch.empty(F * M, dtype=torch.float64, device=dev) if want_power else None
+    with torch.cuda.device(dev):
+        check(lib().pnce_quantize(context(dev).handle, Y.data_ptr(), F, M, N, dt, ws.data_ptr(),
+                                  ws.numel(), exps.data_ptr(), _ptr(power), _stream(dev)),
+              "pnce_quantize")
+    pitch = (N + 63) // 64 * 64
+    eb = {1: 4, 2: 2, 3: 2, 4: 1}[dt]
+    rows = 2 * F * M
+    abytes = rows * pitch * eb
+    view_dt = {4: torch.int32, 2: torch.int16, 1: torch.uint8}[eb]
+    q = ws[:abytes].view(view_dt).view(rows, pitch)
+    sc_off = (abytes + 255) // 256 * 256
+    factor = ws[sc_off:sc_off + 4 * F * M].view(torch.float32)
+    return {"q": q, "factor": factor, "exps": exps, "power": power, "workspace": ws,
+            "pitch": pitch}
+
+
+def correlate_quantized(workspace: torch.Tensor, pilot: Pilot, F, M, K, L, dtype, out=None):
+    """Tensor-core correlation of an operand already produced by quantize()."""
+    dt = _dt(dtype)
+    dev = workspace.device
+    N = pilot.N
+    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    with torch.cuda.device(dev):
+        check(lib().pnce_correlate_quantized(pilot.ctx.handle, pilot.handle, F, M, N, K, L, dt,
+                                             workspace.data_ptr(), workspace.numel(),
+                                             H.data_ptr(), _stream(dev)),
+              "pnce_correlate_quantized")
+    return H
+
+
+def estimate_real_pilot(Y: torch.Tensor, p: torch.Tensor, K: int, L: int, out=None):
+    """FP32 estimate with a real-valued pilot p (float32 CUDA tensor [N])."""
+    F, M, N = _check_y(Y)
+    if p.dtype != torch.float32 or p.shape != (N,) or not p.is_contiguous() or p.device != Y.device:
+        raise ValueError("p must be a contiguous float32 tensor [N] on Y's device")
+    dev = Y.device
+    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    with torch.cuda.device(dev):
+        check(lib().pnce_estimate_real_pilot(context(dev).handle, p.data_ptr(), Y.data_ptr(), F,
+                                             M, N, K, L, H.data_ptr(), _stream(dev)),
+              "pnce_estimate_real_pilot")
+    return H
+
+
+def backward(p: torch.Tensor, Y: torch.Tensor, G: torch.Tensor, K: int, L: int,
+             need_dY=True, need_dp=True):
+    """Adjoint of estimate_real_pilot: (dY [F, M, N] complex64, dp [N] float32)."""
+    F, M, N = _check_y(Y)
+    if G.dtype != torch.complex64 or tuple(G.shape) != (F, M, K, L) or not G.is_contiguous():
+        raise ValueError("G must be a contiguous complex64 tensor [F, M, K, L]")
+    dev = Y.device
+    dY = torch.empty((F, M, N), dtype=torch.complex64, device=dev) if need_dY else None
+    dp = torch.empty(N, dtype=torch.float32, device=dev) if need_dp else None
+    need = backward_workspace_size(F, M, N, K, L) if need_dp else 0
+    ws = _workspace(dev, need, key="bwd")
+    with torch.cuda.device(dev):
+        check(lib().pnce_backward(context(dev).handle, p.data_ptr(), Y.data_ptr(), G.data_ptr(),
+                                  F, M, N, K, L, _ptr(dY), _ptr(dp), _ptr(ws),
+                                  0 if ws is None else ws.numel(), _stream(dev)),
+              "pnce_backward")
+    return dY, dp
+
+
+def estimate_host(Y_host: torch.Tensor, pilot: Pilot, K: int, L: int, dtype="fp32", out=None,
+                  workspace=None) -> torch.Tensor:
+    """End-to-end estimate from a host complex64 tensor (pinned memory recommended).
+
+    The C entry point copies Y to the device, estimates and copies H back, all on the
+    current stream; this call waits for the result.
+    """
+    if Y_host.is_cuda or Y_host.dtype != torch.complex64 or Y_host.dim() != 3:
+        raise ValueError("Y_host must be a host complex64 tensor [F, M, N]")
+    Y_host = Y_host.contiguous()
+    F, M, N = Y_host.shape
+    dt = _dt(dtype)
+    dev = pilot.device
+    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64,
+                                                pin_memory=Y_host.is_pinned())
+    need = host_workspace_size(F, M, N, K, L, dt)
+    ws = workspace if workspace is not None else _workspace(dev, need, key="host")
+    with torch.cuda.device(dev):
+        s = _stream(dev)
+        check(lib().pnce_estimate_host(pilot.ctx.handle, pilot.handle, Y_host.data_ptr(), F, M,
+                                       N, K, L, dt, _ptr(ws), 0 if ws is None else ws.numel(),
+                                       H.data_ptr(), s), "pnce_estimate_host")
+        torch.cuda.current_stream(dev).synchronize()
+    return H

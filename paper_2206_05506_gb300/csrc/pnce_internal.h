@@ -1,0 +1,57 @@
+// Internal declarations shared by the translation units of libpnce (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pnce.h"
+
+struct pnce_handle {
+    int device;
+    int num_sms;
+    int max_smem_optin;
+    int cc_major, cc_minor;
+    int* status_dev;                    // latched device-side status word
+};
+
+struct pnce_pilot {
+    int device;
+    int N;
+    int ext_words;                      // words of the wrapped bit table
+    uint32_t* ext_bits_dev;             // bit t = pilot bit (t mod N), t < 32 * ext_words
+};
+
+namespace pnce {
+
+// Elements of a quantised row are padded to a multiple of this (TMA row pitch).
+constexpr int kRowPad = 64;
+
+inline size_t round_up(size_t x, size_t m) { return (x + m - 1) / m * m; }
+inline int row_pitch(int N) { return (int)round_up((size_t)N, kRowPad); }
+int elem_bytes(int dtype);              // bytes per quantised element (0 for FP32_SIMT)
+
+// Workspace carve-up for the tensor-core path.
+struct QuantLayout {
+    size_t a_offset, a_bytes;           // [2*A][pitch] quantised operand
+    size_t scale_offset;                // float[A]: 2^-s_a / N
+    size_t total;
+};
+QuantLayout quant_layout(long long A, int N, int dtype);
+
+// Launchers (return cudaSuccess or the launch error).
+cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long A, int N,
+                             int KL, float2* H, cudaStream_t s);
+cudaError_t launch_simt_real(const float* p, const float2* Y, long long A, int N, int KL,
+                             float2* H, cudaStream_t s);
+cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* ws,
+                            int32_t* exps, double* power, cudaStream_t s);
+// status: PNCE_OK, or PNCE_ECUDA / PNCE_EUNSUPPORTED
+pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
+                      int KL, int dtype, const void* ws, float2* H, cudaStream_t s);
+cudaError_t launch_backward(const float* p, const float2* Y, const float2* G, long long A,
+                            int N, int KL, float2* dY, float* dp, void* ws, size_t ws_bytes,
+                            cudaStream_t s);
+size_t backward_workspace(long long A, int N, int KL);
+
+}  // namespace pnce

@@ -1,0 +1,199 @@
+// Reduced-precision operand for the tensor-core correlation (Sec. III-B: the received
+// block is converted to the tensor cores' input format before the product).
+//
+// One block per antenna a: pass 1 reduces A_a = max |component| (FP32, exact) and, only
+// when the caller asks for it, E_a = sum |y|^2 in FP64 (squares of FP32 values are exact
+// in FP64; GB300's FP64 rate is low, so the estimate path does not request it); the
+// power-of-two scale 2^s_a is taken from A_a; pass 2 re-reads the row (an L2 hit) and
+// writes rows 2a (real) and 2a+1 (imaginary) of round(y 2^s_a), four samples per thread
+// per step.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "pnce_internal.h"
+
+namespace {
+
+constexpr int THREADS = 256;
+
+template <int DT> struct Fmt;
+template <> struct Fmt<PNCE_FP16> { static constexpr int target = 15; using T = uint16_t; };
+template <> struct Fmt<PNCE_BF16> { static constexpr int target = 0; using T = uint16_t; };
+template <> struct Fmt<PNCE_TF32> { static constexpr int target = 0; using T = uint32_t; };
+template <> struct Fmt<PNCE_FP8E4M3> { static constexpr int target = 8; using T = uint8_t; };
+
+__device__ __forceinline__ uint16_t to_f16(float x) {
+    return __half_as_ushort(__float2half_rn(x));
+}
+__device__ __forceinline__ uint16_t to_bf16(float x) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// two e4m3 codes (lo from a, hi from b), round to nearest even, saturate to +-448
+__device__ __forceinline__ uint16_t to_e4m3x2(float a, float b) {
+    uint16_t r;
+    asm("cvt.rn.satfinite.e4m3x2.f32 %0, %2, %1;" : "=h"(r) : "f"(a), "f"(b));
+    return r;
+}
+
+// write four consecutive converted values v[0..3] at element n of row `row`
+template <int DT>
+__device__ __forceinline__ void store4(void* base, long long row, int pitch, int n,
+                                       const float v[4], int valid) {
+    using T = typename Fmt<DT>::T;
+    T* p = reinterpret_cast<T*>(base) + row * (long long)pitch + n;
+    if constexpr (DT == PNCE_FP16 || DT == PNCE_BF16) {
+        uint16_t c[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[i] = (DT == PNCE_FP16) ? to_f16(v[i]) : to_bf16(v[i]);
+        if (valid == 4) {
+            uint2 w;
+            w.x = c[0] | ((uint32_t)c[1] << 16);
+            w.y = c[2] | ((uint32_t)c[3] << 16);
+            *reinterpret_cast<uint2*>(p) = w;
+        } else {
+            for (int i = 0; i < valid; ++i) p[i] = c[i];
+        }
+    } else if constexpr (DT == PNCE_TF32) {
+        uint32_t c[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) c[i] = to_tf32(v[i]);
+        if (valid == 4) {
+            *reinterpret_cast<uint4*>(p) = make_uint4(c[0], c[1], c[2], c[3]);
+        } else {
+            for (int i = 0; i < valid; ++i) p[i] = c[i];
+        }
+    } else {
+        const uint16_t lo = to_e4m3x2(v[0], v[1]);
+        const uint16_t hi = to_e4m3x2(v[2], v[3]);
+        if (valid == 4) {
+            *reinterpret_cast<uint32_t*>(p) = lo | ((uint32_t)hi << 16);
+        } else {
+            const uint8_t c[4] = {(uint8_t)(lo & 0xff), (uint8_t)(lo >> 8), (uint8_t)(hi & 0xff),
+                                  (uint8_t)(hi >> 8)};
+            for (int i = 0; i < valid; ++i) p[i] = c[i];
+        }
+    }
+}
+
+template <int DT, bool POW>
+__global__ void __launch_bounds__(THREADS)
+quantize_kernel(const float2* __restrict__ Y, long long A, int N, int pitch, void* __restrict__ Q,
+                float* __restrict__ out_scale, int32_t* __restrict__ exps,
+                double* __restrict__ power, float invN) {
+    __shared__ float s_max[THREADS / 32];
+    __shared__ double s_pow[THREADS / 32];
+    __shared__ float s_scale;
+
+    const long long a = blockIdx.x;
+    const float2* row = Y + a * N;
+    const int tid = threadIdx.x;
+
+    float amax = 0.f;
+    double e = 0.0;
+    for (int n = tid; n < N; n += THREADS) {
+        const float2 y = row[n];
+        amax = fmaxf(amax, fmaxf(fabsf(y.x), fabsf(y.y)));
+        if constexpr (POW) e += (double)y.x * (double)y.x + (double)y.y * (double)y.y;
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+        if constexpr (POW) e += __shfl_xor_sync(0xffffffffu, e, o);
+    }
+    if ((tid & 31) == 0) {
+        s_max[tid >> 5] = amax;
+        s_pow[tid >> 5] = e;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        float m = 0.f;
+        double et = 0.0;
+        for (int w = 0; w < THREADS / 32; ++w) {   // fixed order: deterministic
+            m = fmaxf(m, s_max[w]);
+            et += s_pow[w];
+        }
+        int se = 0;
+        if (Fmt<DT>::target != 0 && m > 0.f && isfinite(m)) {
+            int ex;
+            frexpf(m, &ex);                          // m = mant * 2^ex, mant in [0.5, 1)
+            se = Fmt<DT>::target - ex;
+            se = se < -100 ? -100 : (se > 100 ? 100 : se);
+        }
+        s_scale = ldexpf(1.0f, se);
+        out_scale[a] = ldexpf(invN, -se);
+        if (exps) exps[a] = se;
+        if constexpr (POW) power[a] = et / (double)N;
+    }
+    __syncthreads();
+    const float sc = s_scale;
+
+    // pass 2: four consecutive samples per thread per step
+    for (int n = 4 * tid; n < N; n += 4 * THREADS) {
+        const int valid = min(4, N - n);
+        float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < valid) {
+                const float2 y = row[n + i];
+                re[i] = y.x * sc;          // exact: power-of-two scale
+                im[i] = y.y * sc;
+            }
+        }
+        store4<DT>(Q, 2 * a, pitch, n, re, valid);
+        store4<DT>(Q, 2 * a + 1, pitch, n, im, valid);
+    }
+}
+
+template <int DT>
+cudaError_t launch_dt(const float2* Y, long long A, int N, void* ws, int32_t* exps,
+                      double* power, cudaStream_t s) {
+    const pnce::QuantLayout lay = pnce::quant_layout(A, N, DT);
+    unsigned char* base = static_cast<unsigned char*>(ws);
+    const float invN = (float)(1.0 / (double)N);
+    if (A > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    auto kern = power ? quantize_kernel<DT, true> : quantize_kernel<DT, false>;
+    kern<<<(unsigned)A, THREADS, 0, s>>>(Y, A, N, pnce::row_pitch(N), base + lay.a_offset,
+                                         reinterpret_cast<float*>(base + lay.scale_offset),
+                                         exps, power, invN);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace pnce {
+
+int elem_bytes(int dtype) {
+    switch (dtype) {
+        case PNCE_FP16: case PNCE_BF16: return 2;
+        case PNCE_TF32: return 4;
+        case PNCE_FP8E4M3: return 1;
+        default: return 0;
+    }
+}
+
+QuantLayout quant_layout(long long A, int N, int dtype) {
+    QuantLayout l{};
+    l.a_offset = 0;
+    l.a_bytes = (size_t)(2 * A) * (size_t)row_pitch(N) * (size_t)elem_bytes(dtype);
+    l.scale_offset = round_up(l.a_bytes, 256);
+    l.total = round_up(l.scale_offset + (size_t)A * sizeof(float), 256);
+    return l;
+}
+
+cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* ws,
+                            int32_t* exps, double* power, cudaStream_t s) {
+    switch (dtype) {
+        case PNCE_FP16: return launch_dt<PNCE_FP16>(Y, A, N, ws, exps, power, s);
+        case PNCE_BF16: return launch_dt<PNCE_BF16>(Y, A, N, ws, exps, power, s);
+        case PNCE_TF32: return launch_dt<PNCE_TF32>(Y, A, N, ws, exps, power, s);
+        case PNCE_FP8E4M3: return launch_dt<PNCE_FP8E4M3>(Y, A, N, ws, exps, power, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pnce

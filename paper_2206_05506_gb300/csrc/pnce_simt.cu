@@ -1,0 +1,197 @@
+// FP32 correlation on the CUDA cores: H[a][j] = (1/N) sum_n Y[a][n] p[(n - j) mod N]
+// (Eq. 3 / Eq. 10 of the paper, the "plain FP32" estimator).  The same kernel, with the
+// pilot read backwards, is the received-block half of the adjoint:
+// dY[a][n] = (1/N) sum_j G[a][j] p[(n - j) mod N] = (1/N) sum_j G[a][j] p'[(j - n) mod N]
+// with p'[x] = p[-x mod N].  In general: out[a][o] = scale * sum_{k < Kred} in[a][k] *
+// pilot[(k - o) mod Nmod], o < Nout.
+//
+// Block tile: 32 antennas x 256 lags; thread tile: 4 antennas x 8 consecutive lags, so
+// each received sample read from shared memory feeds 64 FMAs.  Because a thread's lags
+// are consecutive, the pilot values it needs at sample n+1 are those of sample n shifted
+// by one lag: a 15-entry register window slides along the pilot, one new shared load per
+// sample.  Received samples and the pilot window of each 128-sample chunk are staged in
+// shared memory, double buffered (cp.async for Y).
+#include "pnce_internal.h"
+
+namespace {
+
+constexpr int RA = 4;             // antennas per thread
+constexpr int RJ = 8;             // consecutive lags per thread
+constexpr int WARPS = 8;
+constexpr int TA = WARPS * RA;    // antennas per block
+constexpr int TJ = 32 * RJ;       // lags per block
+constexpr int NC = 128;           // samples per chunk
+constexpr int ELEN = NC + TJ + 8; // pilot entries staged per chunk
+constexpr int EPAD = ELEN + ELEN / 32 + 4;
+
+// Pilot entries are stored with one pad word per 32 so that lanes reading entries 8 apart
+// hit distinct banks.
+__device__ __forceinline__ int epos(int t) { return t + (t >> 5); }
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    int bytes = valid ? 8 : 0;          // 0 source bytes: zero fill
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+struct Smem {
+    float e[2][EPAD];
+    float2 y[2][TA][NC];
+};
+
+enum Mode { FWD_BITS = 0, FWD_REAL = 1, ADJ_REAL = 2 };
+
+template <int MODE>
+__device__ __forceinline__ float pilot_value(const uint32_t* bits, const float* preal, int q,
+                                             int nmod) {
+    if constexpr (MODE == ADJ_REAL) {
+        return __ldg(preal + (q == 0 ? 0 : nmod - q));
+    } else if constexpr (MODE == FWD_BITS) {
+        uint32_t b = (__ldg(bits + (q >> 5)) >> (q & 31)) & 1u;
+        return b ? -1.0f : 1.0f;
+    } else {
+        return __ldg(preal + q);
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(256, 2)
+simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ preal,
+                 const float2* __restrict__ Y, long long A, int N /* reduction length */,
+                 int KL /* outputs per row */, int nmod, int num_jt, float invN,
+                 float2* __restrict__ H) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long bid = blockIdx.x;
+    const int j0 = (int)(bid % num_jt) * TJ;
+    const long long a0 = (bid / num_jt) * TA;
+    const int nchunks = (N + NC - 1) / NC;
+    // chunk-local pilot entry t holds p[(c*NC + t - (j0 + TJ - 1)) mod N]
+    const long long eoff = (long long)j0 + TJ - 1;
+
+    auto stage = [&](int c, int buf) {
+        const int n0 = c * NC;
+        for (int i = tid; i < TA * NC; i += 256) {
+            const int aa = i / NC, nn = i % NC;
+            const long long a = a0 + aa;
+            const bool ok = (a < A) && (n0 + nn < N);
+            const float2* src = ok ? (Y + a * N + n0 + nn) : Y;
+            cp_async8(&sm.y[buf][aa][nn], src, ok);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+        for (int t = tid; t < ELEN; t += 256) {
+            long long q = ((long long)n0 + t - eoff) % nmod;
+            if (q < 0) q += nmod;
+            sm.e[buf][epos(t)] = pilot_value<MODE>(bits, preal, (int)q, nmod);
+        }
+    };
+
+    float2 acc[RA][RJ];
+#pragma unroll
+    for (int i = 0; i < RA; ++i)
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) acc[i][r] = make_float2(0.f, 0.f);
+
+    // lag of (lane, r) is j0 + 8*lane + r; chunk-local entry for sample n0+u is
+    // u + base - r with base = TJ - 1 - 8*lane (>= 7)
+    const int base = TJ - 1 - RJ * lane;
+
+    stage(0, 0);
+    cp_async_wait_all();
+    __syncthreads();
+
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunks) stage(c + 1, buf ^ 1);
+
+        const float* e = sm.e[buf];
+        float w[15];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) w[i] = e[epos(base - 7 + i)];
+
+#pragma unroll 1
+        for (int s = 0; s < NC / 8; ++s) {
+            float nw[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) nw[i] = e[epos(8 * s + 8 + base + i)];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                float2 y[RA];
+#pragma unroll
+                for (int i = 0; i < RA; ++i) y[i] = sm.y[buf][warp * RA + i][8 * s + u];
+#pragma unroll
+                for (int r = 0; r < RJ; ++r) {
+                    const float pv = w[u - r + 7];
+#pragma unroll
+                    for (int i = 0; i < RA; ++i) {
+                        acc[i][r].x = fmaf(pv, y[i].x, acc[i][r].x);
+                        acc[i][r].y = fmaf(pv, y[i].y, acc[i][r].y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 7; ++i) w[i] = w[i + 8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[7 + i] = nw[i];
+        }
+        cp_async_wait_all();
+        __syncthreads();
+    }
+
+#pragma unroll
+    for (int i = 0; i < RA; ++i) {
+        const long long a = a0 + warp * RA + i;
+        if (a >= A) continue;
+        float2* hrow = H + a * KL;
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) {
+            const int j = j0 + RJ * lane + r;
+            if (j < KL) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
+        }
+    }
+}
+
+template <int MODE>
+cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, long long A,
+                   int N, int KL, int nmod, float2* H, cudaStream_t s) {
+    const int num_jt = (KL + TJ - 1) / TJ;
+    const long long blocks = (long long)num_jt * ((A + TA - 1) / TA);
+    if (blocks <= 0) return cudaSuccess;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const size_t smem = sizeof(Smem);
+    cudaError_t e = cudaFuncSetAttribute(simt_corr_kernel<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const float invN = (float)(1.0 / (double)nmod);
+    simt_corr_kernel<MODE><<<(unsigned)blocks, 256, smem, s>>>(bits, preal, Y, A, N, KL, nmod,
+                                                               num_jt, invN, H);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+namespace pnce {
+
+cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long A, int N,
+                             int KL, float2* H, cudaStream_t s) {
+    return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Y, A, N, KL, N, H, s);
+}
+
+cudaError_t launch_simt_real(const float* p, const float2* Y, long long A, int N, int KL,
+                             float2* H, cudaStream_t s) {
+    return launch<FWD_REAL>(nullptr, p, Y, A, N, KL, N, H, s);
+}
+
+cudaError_t launch_adjoint_dy(const float* p, const float2* G, long long A, int N, int KL,
+                              float2* dY, cudaStream_t s) {
+    // reduction over the KL lags of G, N outputs per row, pilot read backwards
+    return launch<ADJ_REAL>(nullptr, p, G, A, KL, N, N, dY, s);
+}
+
+}  // namespace pnce

@@ -1,0 +1,595 @@
+// Tensor-core correlation (Sec. III-B: the correlator of Eq. 3 / Eq. 10 as a matrix
+// product on the tensor cores) for sm_103a: tcgen05.mma with FP32 accumulators in TMEM.
+//
+//   C[r][j] = sum_n A[r][n] * B[n][j],  B[n][j] = p[(n - j) mod N]  (the circulant, Eq. 2)
+//
+// A: the quantised received block, rows r = 2a (real) / 2a+1 (imaginary) of antenna a,
+//    staged 128 rows x 128 B per pipeline stage by TMA with the 128-byte swizzle.
+// B: never stored in HBM.  The lag order inside a tile is reversed (tile column i holds
+//    lag j0 + BN - 1 - i), which turns the Toeplitz tile into a Hankel one: the value at
+//    (column 8q + r, sample n0 + EPR*t + c) is p[(s + G*(QS*q + TS*t) + r + c) mod N].
+//    Every 8-row x 16-byte core matrix of the canonical no-swizzle K-major layout is then
+//    one of a short list indexed by D = QS*q + TS*t, so the pilot operand of a stage is
+//    that list alone (<= 70 core matrices, <= 9 KB), generated from the packed pilot bits
+//    by one warp, and the shared-memory descriptor's two core-matrix strides (LBO along K,
+//    SBO along the lags) point into it with overlap.
+// Epilogue: tcgen05.ld of 32 accumulator columns, re/im pairing by lane shuffles (rows 2a,
+//    2a+1 are adjacent TMEM lanes), the per-antenna factor 2^-s_a / N, lag order restored,
+//    staged through a bank-conflict-free swizzled buffer and written as whole 256-byte
+//    rows of H.  TMEM holds two 256-column accumulators so the epilogue of one tile
+//    overlaps the products of the next.
+//
+// Warp roles (256 threads, persistent, one CTA per SM): warp 0 TMA producer, warp 1 pilot
+// tile generator, warp 2 TMEM allocator + MMA issuer, warps 4-7 epilogue (TMEM lane
+// quarter = warp % 4).  Tiles t = blockIdx.x + i*gridDim.x map to (row block t / num_jt,
+// lag block t % num_jt); with a grid that is a multiple of num_jt a CTA keeps one lag block
+// and the CTAs sharing a row block run together, so A is read from HBM about once.
+//
+// Every mbarrier wait is bounded in time; on expiry the CTA latches PNCE_ETIMEOUT, all
+// roles leave their loops, in-flight TMA loads and MMAs are drained (bounded), TMEM is
+// freed and the kernel returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "pnce_internal.h"
+
+namespace {
+
+constexpr int THREADS = 256;
+constexpr int BM = 128;                   // accumulator rows (TMEM lanes) per tile
+constexpr int STAGES = 8;
+constexpr int A_STAGE = BM * 128;         // 16 KB
+constexpr int ACC_COLS = 256;
+constexpr int TMEM_COLS = 512;
+constexpr int MAX_BN = 256;
+constexpr int EPI_BYTES = 4 * 4096;       // 4 warps x (16 antennas x 32 lags x 8 B)
+
+struct TcParams {
+    int N;
+    int KL;
+    long long A;            // antennas
+    int BN;                 // lags per tile (multiple of 32, <= 256)
+    int num_jt;             // lag blocks
+    long long num_tiles;
+    int num_kb;             // pipeline stages per tile (K blocks)
+    unsigned long long wait_limit_ns;
+    int* err;
+};
+
+template <int DT> struct TcFmt;
+// BK: elements per 128-byte A row; EPR: elements per 16-byte core-matrix row;
+// G: pilot offset per core-matrix index step; QS/TS: index step per lag / K core matrix.
+template <> struct TcFmt<PNCE_FP16> {
+    static constexpr int BK = 64, EPR = 8, G = 8, QS = 1, TS = 1;
+    static constexpr uint32_t AB = (0u << 7) | (0u << 10);
+};
+template <> struct TcFmt<PNCE_BF16> {
+    static constexpr int BK = 64, EPR = 8, G = 8, QS = 1, TS = 1;
+    static constexpr uint32_t AB = (1u << 7) | (1u << 10);
+};
+template <> struct TcFmt<PNCE_FP8E4M3> {
+    static constexpr int BK = 128, EPR = 16, G = 8, QS = 1, TS = 2;
+    static constexpr uint32_t AB = (0u << 7) | (0u << 10);
+};
+template <> struct TcFmt<PNCE_TF32> {
+    static constexpr int BK = 32, EPR = 4, G = 4, QS = 2, TS = 1;
+    static constexpr uint32_t AB = (2u << 7) | (2u << 10);
+};
+
+template <int DT>
+constexpr int ncm(int bn) {   // core matrices of one stage's pilot operand
+    using F = TcFmt<DT>;
+    return (bn / 8 - 1) * F::QS + (F::BK / F::EPR - 1) * F::TS + 1;
+}
+template <int DT>
+constexpr int b_stage_bytes() { return (ncm<DT>(MAX_BN) * 128 + 1023) / 1024 * 1024; }
+
+struct Ctl {
+    unsigned long long full_a[STAGES];
+    unsigned long long full_b[STAGES];
+    unsigned long long empty[STAGES];
+    unsigned long long tfull[2];
+    unsigned long long tempty[2];
+    uint32_t tmem_base;
+    int abort_flag;
+};
+
+template <int DT>
+constexpr size_t smem_bytes() {
+    return 1024 /* alignment slack */ + (size_t)STAGES * A_STAGE +
+           (size_t)STAGES * b_stage_bytes<DT>() + EPI_BYTES + sizeof(Ctl);
+}
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long gtime() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.b32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity` of barrier b.  honor_abort: give up as
+// soon as another role has latched an abort.  Returns false when the wait was abandoned.
+__device__ __noinline__ bool wait_bar(unsigned long long* b, uint32_t parity, Ctl* ctl,
+                                      const TcParams& prm, bool honor_abort) {
+    if (mbar_test(b, parity)) return true;
+    const unsigned long long t0 = gtime();
+    for (;;) {
+        if (mbar_test(b, parity)) return true;
+        if (honor_abort && *(volatile int*)&ctl->abort_flag) return false;
+        if (gtime() - t0 > prm.wait_limit_ns) {
+            *(volatile int*)&ctl->abort_flag = 1;
+            atomicCAS(prm.err, 0, (int)PNCE_ETIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05 format: start >> 4 in bits 0-13, leading
+// byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, version 1 in 46-47,
+// layout type in 61-63: 0 = no swizzle, 2 = 128-byte swizzle).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo,
+                                          uint32_t layout) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)layout << 61;
+    return d;
+}
+
+template <int DT>
+__device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accumulate) {
+    if constexpr (DT == PNCE_FP16 || DT == PNCE_BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if constexpr (DT == PNCE_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_commit(unsigned long long* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            su32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// --------------------------------------------------------- pilot operand tiles
+
+// 16 bytes holding EPR consecutive +-1 pilot values in the operand format, from the low
+// EPR bits of x (bit c -> element c; bit 0 -> +1, bit 1 -> -1).
+template <int DT>
+__device__ __forceinline__ uint4 pilot_row(uint32_t x) {
+    uint32_t w[4];
+    if constexpr (DT == PNCE_FP16 || DT == PNCE_BF16) {
+        constexpr uint32_t one = (DT == PNCE_FP16) ? 0x3C00u : 0x3F80u;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t b0 = (x >> (2 * i)) & 1u, b1 = (x >> (2 * i + 1)) & 1u;
+            w[i] = (one | (b0 << 15)) | ((one | (b1 << 15)) << 16);
+        }
+    } else if constexpr (DT == PNCE_FP8E4M3) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t nib = (x >> (4 * i)) & 0xFu;
+            w[i] = 0x38383838u | ((nib & 1u) << 7) | ((nib & 2u) << 14) | ((nib & 4u) << 21) |
+                   ((nib & 8u) << 28);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) w[i] = 0x3F800000u | (((x >> i) & 1u) << 31);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Pilot operand of one stage: core matrix D, row r (byte offset 128 D + 16 r) holds the
+// EPR pilot values starting at sequence index s_start + G*D + r (mod N).
+template <int DT>
+__device__ __forceinline__ void gen_pilot_stage(unsigned char* dst, const uint32_t* __restrict__ ext,
+                                                int N, long long s_start, int rows, int lane) {
+    using F = TcFmt<DT>;
+    // row index idx = 8 D + r: sequence offset G*(idx >> 3) + (idx & 7); lanes step by 32
+    // rows, i.e. by 4 core matrices = 4 G sequence positions
+    long long w0 = s_start + (long long)F::G * (lane >> 3) + (lane & 7);
+    int pos = (int)(((w0 % N) + N) % N);
+    constexpr int step = 4 * F::G;
+    for (int idx = lane; idx < rows; idx += 32) {
+        const uint32_t lo = __ldg(ext + (pos >> 5)), hi = __ldg(ext + (pos >> 5) + 1);
+        const uint64_t win = (((uint64_t)hi << 32) | lo) >> (pos & 31);
+        const uint4 v = pilot_row<DT>((uint32_t)win);
+        *reinterpret_cast<uint4*>(dst + (idx >> 3) * 128 + (idx & 7) * 16) = v;
+        pos += step;
+        while (pos >= N) pos -= N;
+    }
+}
+
+// ------------------------------------------------------------------- the kernel
+
+template <int DT>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
+               const float* __restrict__ row_scale, float2* __restrict__ H, const TcParams prm) {
+    using F = TcFmt<DT>;
+    constexpr int BSTAGE = b_stage_bytes<DT>();
+    constexpr int KSTEPS = 4;                  // MMAs per stage: 128 B of K, 32 B each
+    constexpr uint32_t LBO = 128u * F::TS, SBO = 128u * F::QS;
+    constexpr uint32_t KSTEP_B = 2u * 128u * F::TS;       // B bytes per MMA K step
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* sA = base;
+    unsigned char* sB = sA + STAGES * A_STAGE;
+    float4* sEpi = reinterpret_cast<float4*>(sB + STAGES * BSTAGE);
+    Ctl* ctl = reinterpret_cast<Ctl*>(reinterpret_cast<unsigned char*>(sEpi) + EPI_BYTES);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int BN = prm.BN, num_jt = prm.num_jt, num_kb = prm.num_kb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&ctl->full_a[s], 1);
+            mbar_init(&ctl->full_b[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl->tfull[b], 1);
+            mbar_init(&ctl->tempty[b], 4);
+        }
+        ctl->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
+                     : "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&ctl->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t stage = 0, phase = 0;
+            long long issued = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < prm.num_tiles && ok; t += gridDim.x) {
+                const int y = (int)(t / num_jt) * BM;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!wait_bar(&ctl->empty[stage], phase ^ 1u, ctl, prm, true)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_tx(&ctl->full_a[stage], A_STAGE);
+                    tma_load_2d(sA + stage * A_STAGE, &tmap, kb * F::BK, y, &ctl->full_a[stage]);
+                    ++issued;
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                }
+            }
+            // drain: the last loads issued must have landed before the CTA may exit
+            const long long first = issued > STAGES ? issued - STAGES : 0;
+            for (long long i = first; i < issued; ++i)
+                wait_bar(&ctl->full_a[i % STAGES], (uint32_t)((i / STAGES) & 1), ctl, prm, false);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------- pilot operand generator
+        const int rows = ncm<DT>(BN) * 8;
+        uint32_t stage = 0, phase = 0;
+        bool ok = true;
+        for (long long t = blockIdx.x; t < prm.num_tiles && ok; t += gridDim.x) {
+            const long long j0 = (long long)(t % num_jt) * BN;
+            for (int kb = 0; kb < num_kb; ++kb) {
+                int got = 1;
+                if (lane == 0) got = wait_bar(&ctl->empty[stage], phase ^ 1u, ctl, prm, true);
+                got = __shfl_sync(0xffffffffu, got, 0);
+                if (!got) { ok = false; break; }
+                const long long s_start = (long long)kb * F::BK - j0 - BN + 1;
+                gen_pilot_stage<DT>(sB + stage * BSTAGE, ext, prm.N, s_start, rows, lane);
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&ctl->full_b[stage]);
+                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | F::AB | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
+            uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
+            unsigned long long* last_bar = nullptr;
+            uint32_t last_par = 0;
+            bool ok = true;
+            for (long long t = blockIdx.x; t < prm.num_tiles && ok; t += gridDim.x) {
+                if (!wait_bar(&ctl->tempty[acc], acc_phase ^ 1u, ctl, prm, true)) break;
+                fence_after();
+                const uint32_t d = tmem + acc * ACC_COLS;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!wait_bar(&ctl->full_a[stage], phase, ctl, prm, true) ||
+                        !wait_bar(&ctl->full_b[stage], phase, ctl, prm, true)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t a0 = su32(sA + stage * A_STAGE);
+                    const uint32_t b0 = su32(sB + stage * BSTAGE);
+#pragma unroll
+                    for (int ks = 0; ks < KSTEPS; ++ks) {
+                        const uint64_t ad = sdesc(a0 + 32u * ks, 16u, 1024u, 2u);
+                        const uint64_t bd = sdesc(b0 + KSTEP_B * ks, LBO, SBO, 0u);
+                        umma<DT>(d, ad, bd, idesc, (kb | ks) != 0);
+                    }
+                    umma_commit(&ctl->empty[stage]);
+                    last_bar = &ctl->empty[stage];
+                    last_par = phase;
+                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                umma_commit(&ctl->tfull[acc]);
+                last_bar = &ctl->tfull[acc];
+                last_par = acc_phase;
+                acc ^= 1u;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            if (last_bar) wait_bar(last_bar, last_par, ctl, prm, false);   // drain the MMAs
+        }
+    } else if (warp >= 4) {
+        // --------------------------------------------------------------- epilogue
+        const int q = warp & 3;                 // TMEM lane quarter
+        const int half = lane & 1, ant_l = lane >> 1;
+        float4* stg = sEpi + q * 256;
+        uint32_t acc = 0, acc_phase = 0;
+        for (long long t = blockIdx.x; t < prm.num_tiles; t += gridDim.x) {
+            const long long rb = t / num_jt;
+            const int j0 = (int)(t % num_jt) * BN;
+            int got = 1;
+            if (lane == 0) got = wait_bar(&ctl->tfull[acc], acc_phase, ctl, prm, true);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) break;
+            fence_after();
+            const long long ant_base = rb * (BM / 2) + q * 16;
+            const long long my_ant = ant_base + ant_l;
+            const float rs = (my_ant < prm.A) ? __ldg(row_scale + my_ant) : 0.f;
+            const int nch = BN / 32;
+            for (int c = 0; c < nch; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * ACC_COLS + 32 * c, v);
+                if (c == nch - 1) {
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
+                }
+                // column 32c + i holds lag jlo + 31 - i; this lane keeps 16 lags of its
+                // antenna: lags jlo + 16*half + i, i < 16
+                float re[16], im[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float lo = __uint_as_float(v[31 - i]);      // lag jlo + i
+                    const float hi = __uint_as_float(v[15 - i]);      // lag jlo + 16 + i
+                    const float send = half ? lo : hi;
+                    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                    re[i] = (half ? recv : lo) * rs;
+                    im[i] = (half ? hi : recv) * rs;
+                }
+                // staging: row ant_l (256 B = 16 chunks of 2 complex), chunk 8*half + k
+                // stored at (8*half + k) ^ ((ant_l & 3) << 1 | half)
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int lc = 8 * half + k;
+                    const int pc = lc ^ (((ant_l & 3) << 1) | half);
+                    stg[ant_l * 16 + pc] =
+                        make_float4(re[2 * k], im[2 * k], re[2 * k + 1], im[2 * k + 1]);
+                }
+                __syncwarp();
+                const int jlo = j0 + BN - 32 - 32 * c;
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int row = 2 * it + (lane >> 4), lc = lane & 15;
+                    const int pc = lc ^ (((row & 3) << 1) | (lc >> 3));
+                    const float4 val = stg[row * 16 + pc];
+                    const long long ant = ant_base + row;
+                    const int j = jlo + 2 * lc;
+                    if (ant < prm.A && j < prm.KL) {
+                        float2* dst = H + ant * prm.KL + j;
+                        if (j + 1 < prm.KL && ((ant * prm.KL) & 1) == 0) {
+                            *reinterpret_cast<float4*>(dst) = val;
+                        } else {
+                            dst[0] = make_float2(val.x, val.y);
+                            if (j + 1 < prm.KL) dst[1] = make_float2(val.z, val.w);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            acc ^= 1u;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// ------------------------------------------------------------------------- host
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+unsigned long long wait_limit_ns() {
+    static unsigned long long v = [] {
+        const char* e = getenv("PNCE_WAIT_LIMIT_MS");
+        long long ms = e ? atoll(e) : 2000;
+        if (ms < 1) ms = 1;
+        return (unsigned long long)ms * 1000000ull;
+    }();
+    return v;
+}
+
+template <int DT>
+pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N, int KL,
+                      const void* ws, float2* H, cudaStream_t s) {
+    using F = TcFmt<DT>;
+    auto enc = encode_fn();
+    if (!enc) return PNCE_ECUDA;
+    const pnce::QuantLayout lay = pnce::quant_layout(A, N, DT);
+    const unsigned char* wsb = static_cast<const unsigned char*>(ws);
+
+    CUtensorMap map;
+    CUtensorMapDataType ty = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    if (DT == PNCE_BF16) ty = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    if (DT == PNCE_FP8E4M3) ty = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    if (DT == PNCE_TF32) ty = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)(2 * A)};
+    const cuuint64_t strides[1] = {(cuuint64_t)pnce::row_pitch(N) * pnce::elem_bytes(DT)};
+    const cuuint32_t box[2] = {(cuuint32_t)F::BK, (cuuint32_t)BM};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&map, ty, 2, const_cast<unsigned char*>(wsb + lay.a_offset), dims, strides,
+                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return PNCE_ECUDA;
+
+    TcParams prm;
+    prm.N = N;
+    prm.KL = KL;
+    prm.A = A;
+    prm.num_jt = (KL + MAX_BN - 1) / MAX_BN;
+    const int per = (KL + prm.num_jt - 1) / prm.num_jt;
+    prm.BN = (per + 31) / 32 * 32;
+    const long long num_rb = (2 * A + BM - 1) / BM;
+    prm.num_tiles = num_rb * prm.num_jt;
+    prm.num_kb = (N + F::BK - 1) / F::BK;
+    prm.wait_limit_ns = wait_limit_ns();
+    prm.err = h->status_dev;
+
+    long long grid = h->num_sms;
+    if (grid >= prm.num_jt) grid = grid / prm.num_jt * prm.num_jt;
+    if (grid > prm.num_tiles) grid = prm.num_tiles;
+    if (grid < 1) return PNCE_OK;
+
+    const size_t smem = smem_bytes<DT>();
+    if ((int)smem > h->max_smem_optin) return PNCE_EUNSUPPORTED;
+    if (cudaFuncSetAttribute(tc_corr_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return PNCE_ECUDA;
+    tc_corr_kernel<DT><<<(unsigned)grid, THREADS, smem, s>>>(
+        map, pilot->ext_bits_dev, reinterpret_cast<const float*>(wsb + lay.scale_offset), H, prm);
+    return cudaGetLastError() == cudaSuccess ? PNCE_OK : PNCE_ECUDA;
+}
+
+}  // namespace
+
+namespace pnce {
+
+pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N, int KL,
+                      int dtype, const void* ws, float2* H, cudaStream_t s) {
+    if (!(h->cc_major == 10 && h->cc_minor == 3)) return PNCE_EUNSUPPORTED;
+    switch (dtype) {
+        case PNCE_FP16: return launch_dt<PNCE_FP16>(h, pilot, A, N, KL, ws, H, s);
+        case PNCE_BF16: return launch_dt<PNCE_BF16>(h, pilot, A, N, KL, ws, H, s);
+        case PNCE_FP8E4M3: return launch_dt<PNCE_FP8E4M3>(h, pilot, A, N, KL, ws, H, s);
+        case PNCE_TF32: return launch_dt<PNCE_TF32>(h, pilot, A, N, KL, ws, H, s);
+        default: return PNCE_EINVAL;
+    }
+}
+
+}  // namespace pnce

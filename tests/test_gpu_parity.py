@@ -1,0 +1,199 @@
+"""GPU parity of every estimator path against the FP64 oracle, through the C ABI.
+
+Tolerances (NMSE = sum|gpu - ref|^2 / sum|ref|^2 over the launch):
+* against the oracle on the unquantised complex64 input (the stated accuracy targets):
+  1e-6 for the FP32 paths (SIMT, TF32), 2e-3 for FP16/BF16, 3e-2 for FP8-e4m3;
+* against the oracle applied to the quantised operand (isolates the FP32 accumulation of
+  the tensor-core product from the input rounding): 1e-9 for fp16/bf16/tf32 and 1e-6
+  for e4m3 (whose accumulation inside the tensor core may keep fewer bits);
+* the quantiser itself is integer/byte work and must match bit for bit.
+Output buffers carry guard words on both sides, checked after every launch.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import pn_oracle as O
+from synth import channel as C
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-6, "tf32": 1e-6, "fp16": 2e-3, "bf16": 2e-3, "e4m3": 3e-2}
+TOL_Q = {"tf32": 1e-9, "fp16": 1e-9, "bf16": 1e-9, "e4m3": 1e-6}
+TC = ["fp16", "bf16", "e4m3", "tf32"]
+GUARD = 64
+SENT = complex(12345.0, -777.0)
+
+# (r, M, K, L, F): tiny; the small FP32 case; ragged multi-tile; full lag K*L = N; a
+# K = L = 1 degenerate; many K blocks and lag tiles
+SHAPES = [(3, 1, 1, 1, 1), (7, 8, 2, 16, 1), (6, 3, 7, 9, 2), (10, 100, 5, 60, 3),
+          (12, 64, 16, 128, 2), (5, 2, 31, 1, 1), (8, 65, 3, 85, 1)]
+
+
+@pytest.fixture(scope="module")
+def pk():
+    import paper_2206_05506_gb300 as pk
+    pk.lib()
+    return pk
+
+
+def _case(r, M, K, L, F, seed=0, snr=10.0):
+    w = C.Workload("t", r=r, M=M, K=K, L=L, F=F, snr_db=(snr,), seed=seed)
+    return C.make(w)
+
+
+def _guarded(shape, dev):
+    n = int(np.prod(shape))
+    buf = torch.full((n + 2 * GUARD,), SENT, dtype=torch.complex64, device=dev)
+    return buf, buf[GUARD:GUARD + n].view(*shape)
+
+
+def _guards_ok(buf):
+    g = torch.cat([buf[:GUARD], buf[-GUARD:]]).cpu().numpy()
+    return bool(np.all(g == np.complex64(SENT)))
+
+
+def _run(pk, Y, bits, K, L, dtype):
+    dev = torch.device("cuda", 0)
+    pilot = pk.Pilot(bits, device=dev)
+    F, M, N = Y.shape
+    buf, H = _guarded((F, M, K, L), dev)
+    pk.estimate(torch.from_numpy(Y).to(dev), pilot, K, L, dtype=dtype, out=H)
+    assert pk.get_status(dev) == 0
+    assert _guards_ok(buf), "write outside H"
+    return H.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_fp32_simt_matches_oracle(pk, shape):
+    r, M, K, L, F = shape
+    bits, _, Y = _case(*shape)
+    H = _run(pk, Y, bits, K, L, "fp32")
+    ref = O.estimate(Y, bits, K, L)
+    assert O.nmse(H, ref) <= TOL["fp32"]
+    assert np.abs(H - ref).max() <= 1e-5 * max(1.0, np.abs(ref).max())
+
+
+@pytest.mark.parametrize("dtype", TC)
+@pytest.mark.parametrize("shape", SHAPES)
+def test_tensor_core_matches_oracle(pk, shape, dtype):
+    r, M, K, L, F = shape
+    bits, _, Y = _case(*shape, seed=r)
+    H = _run(pk, Y, bits, K, L, dtype)
+    ref = O.estimate(Y, bits, K, L)
+    refq = O.estimate_quantized(Y, bits, K, L, dtype)
+    assert O.nmse(H, refq) <= TOL_Q[dtype], "accumulation error beyond FP32"
+    assert O.nmse(H, ref) <= TOL[dtype]
+
+
+def _decode(q, dtype):
+    q = q.cpu()
+    if dtype == "fp16":
+        return q.view(torch.float16).double().numpy()
+    if dtype == "bf16":
+        return q.view(torch.bfloat16).double().numpy()
+    if dtype == "tf32":
+        return q.view(torch.float32).double().numpy()
+    return q.view(torch.float8_e4m3fn).double().numpy()
+
+
+@pytest.mark.parametrize("dtype", TC)
+@pytest.mark.parametrize("shape", [(7, 8, 2, 16, 1), (10, 33, 1, 1, 2), (4, 3, 1, 1, 1)])
+def test_quantizer_bit_exact(pk, shape, dtype):
+    r, M, K, L, F = shape
+    bits, _, Y = _case(*shape, seed=5, snr=0.0)
+    # spread the antennas' powers over decades so the scales differ
+    Y = (Y * np.logspace(-3, 3, M, dtype=np.float32)[None, :, None]).astype(np.complex64)
+    dev = torch.device("cuda", 0)
+    res = pk.quantize(torch.from_numpy(Y).to(dev), dtype, want_power=True)
+    Q, se = O.quantize(Y, dtype)
+    N = Y.shape[2]
+    got = _decode(res["q"], dtype)[:, :N].reshape(F * M, 2, N)
+    want = np.stack([Q.real, Q.imag], axis=1).reshape(F * M, 2, N)
+    assert np.array_equal(got, want)
+    assert np.array_equal(res["exps"].cpu().numpy(), se.reshape(-1))
+    fac = np.float32(1.0 / N) * np.ldexp(np.float32(1.0), -se.reshape(-1)).astype(np.float32)
+    assert np.array_equal(res["factor"].cpu().numpy(), fac)
+    pw = (np.abs(Y.astype(np.complex128)) ** 2).mean(axis=-1).reshape(-1)
+    assert np.allclose(res["power"].cpu().numpy(), pw, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("dtype", ["fp32"] + TC)
+def test_paper_scale_workload(pk, dtype):
+    # 128 frames of M=64, N=1023, K=8, L=64 at SNR 0/10/20 dB
+    w = C.PAPER_SCALE
+    bits, h, Y = C.make(w)
+    H = _run(pk, Y, bits, w.K, w.L, dtype)
+    ref = O.estimate(Y, bits, w.K, w.L)
+    assert O.nmse(H, ref) <= TOL[dtype]
+
+
+def test_noise_free_recovery_closed_form(pk):
+    # Eq. 1-3: a noise-free block is estimated as h + (h - S)/N
+    w = C.Workload("nf", r=10, M=16, K=8, L=64, F=2, snr_db=(0.0,), seed=4)
+    bits, h, Y = C.make(w, noise=False)
+    N = w.N
+    x = h.reshape(w.F, w.M, -1)
+    want = (x + (x - x.sum(-1, keepdims=True)) / N).reshape(h.shape)
+    for dtype, tol in (("fp32", 1e-10), ("tf32", 1e-6), ("fp16", 1e-6)):
+        H = _run(pk, Y, bits, w.K, w.L, dtype)
+        assert O.nmse(H, want) <= tol, dtype
+
+
+def test_real_pilot_forward_and_adjoint(pk):
+    dev = torch.device("cuda", 0)
+    rng = np.random.default_rng(1)
+    for (F, M, N, K, L) in [(2, 3, 31, 2, 5), (3, 40, 1023, 8, 64), (1, 5, 300, 3, 100)]:
+        Y = (rng.standard_normal((F, M, N)) + 1j * rng.standard_normal((F, M, N))).astype(np.complex64)
+        p = np.tanh(rng.standard_normal(N)).astype(np.float32)
+        G = (rng.standard_normal((F, M, K, L)) + 1j * rng.standard_normal((F, M, K, L))).astype(np.complex64)
+        Yd, pd, Gd = (torch.from_numpy(a).to(dev) for a in (Y, p, G))
+        H = pk.estimate_real_pilot(Yd, pd, K, L).cpu().numpy()
+        assert O.nmse(H, O.estimate_real_pilot(Y, p.astype(np.float64), K, L)) <= 1e-10
+        dY, dp = pk.backward(pd, Yd, Gd, K, L)
+        rdY, rdp = O.adjoint(G, Y, p.astype(np.float64), K, L)
+        assert O.nmse(dY.cpu().numpy(), rdY) <= 1e-10
+        assert O.nmse(dp.cpu().numpy(), rdp) <= 1e-10
+        # deterministic: a second run is bitwise identical
+        dY2, dp2 = pk.backward(pd, Yd, Gd, K, L)
+        assert torch.equal(dp, dp2) and torch.equal(dY, dY2)
+
+
+def test_deterministic_and_independent_of_batch(pk):
+    # results per frame do not depend on the other frames of the launch
+    bits, _, Y = _case(10, 64, 8, 64, 6, seed=8)
+    dev = torch.device("cuda", 0)
+    pilot = pk.Pilot(bits, device=dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    for dtype in ["fp32"] + TC:
+        full = pk.estimate(Yd, pilot, 8, 64, dtype=dtype)
+        again = pk.estimate(Yd, pilot, 8, 64, dtype=dtype)
+        part = pk.estimate(Yd[2:5].contiguous(), pilot, 8, 64, dtype=dtype)
+        assert torch.equal(full, again)
+        assert torch.equal(full[2:5], part)
+
+
+def test_invalid_arguments(pk):
+    dev = torch.device("cuda", 0)
+    bits, _, Y = _case(7, 4, 2, 16, 1)
+    pilot = pk.Pilot(bits, device=dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    with pytest.raises(pk.PnceError) as e:
+        pk.estimate(Yd, pilot, 8, 16)                       # K*L > N (Eq. 7)
+    assert e.value.status == 1
+    flat = torch.zeros(Y.size + 1, dtype=torch.complex64, device=dev)
+    mis = flat[1:].view(Y.shape)                            # 8-byte aligned only
+    with pytest.raises(pk.PnceError) as e:
+        pk.estimate(mis, pilot, 2, 16)
+    assert e.value.status == 1
+    other = pk.Pilot(bits[:63], device=dev)
+    lib = pk.lib()
+    H = torch.empty((1, 4, 2, 16), dtype=torch.complex64, device=dev)
+    st = lib.pnce_estimate(other.ctx.handle, other.handle, Yd.data_ptr(), 1, 4, 127, 2, 16, 0,
+                           None, 0, H.data_ptr(), None)
+    assert st == 6                                          # pilot length mismatch
+    ws = torch.empty(16, dtype=torch.uint8, device=dev)
+    st = lib.pnce_estimate(pilot.ctx.handle, pilot.handle, Yd.data_ptr(), 1, 4, 127, 2, 16, 2,
+                           ws.data_ptr(), 16, H.data_ptr(), None)
+    assert st == 1                                          # workspace too small
+    assert pk.get_status(dev) == 0

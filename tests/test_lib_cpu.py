@@ -1,0 +1,75 @@
+"""Host-side checks of the C ABI library that need no GPU: it builds, loads, exports
+every function include/pnce.h declares, and its pure host functions behave."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pnce.h")
+
+
+@pytest.fixture(scope="session")
+def lib():
+    from paper_2206_05506_gb300 import _lib, build
+
+    if not os.path.exists(build.LIB_PATH):
+        build.build()
+    return _lib.load()
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pnce_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for must in ("pnce_estimate", "pnce_pilot_create", "pnce_quantize", "pnce_backward",
+                 "pnce_correlate_quantized", "pnce_estimate_real_pilot", "pnce_estimate_host"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_signatures_cover_header(lib):
+    from paper_2206_05506_gb300 import _lib
+
+    assert set(_lib.exported_names()) == set(header_functions())
+
+
+def test_status_strings_and_version(lib):
+    assert lib.pnce_version() >= 10000
+    for s in range(7):
+        assert lib.pnce_status_string(s).startswith(b"PNCE_")
+    assert lib.pnce_status_string(99).startswith(b"PNCE_?")
+
+
+def test_workspace_size_rules(lib):
+    # FP32 SIMT needs no workspace; invalid shapes (Eq. 7: K*L > N) give 0
+    assert lib.pnce_workspace_size(1, 8, 127, 2, 16, 0) == 0
+    assert lib.pnce_workspace_size(1, 8, 127, 8, 16, 2) == 0
+    assert lib.pnce_workspace_size(0, 8, 127, 2, 16, 2) == 0
+    assert lib.pnce_workspace_size(1, 8, 127, 2, 16, 99) == 0
+    # fp16: 2*F*M rows of ceil(N/64)*64 halfs, then F*M float factors, 256-byte rounded
+    F, M, N = 3, 5, 1023
+    rows, pitch = 2 * F * M, 1024
+    a = rows * pitch * 2
+    want = ((a + 255) // 256 * 256 + 4 * F * M + 255) // 256 * 256
+    assert lib.pnce_workspace_size(F, M, N, 8, 64, 2) == want
+    assert lib.pnce_workspace_size(F, M, N, 8, 64, 1) > lib.pnce_workspace_size(F, M, N, 8, 64, 2)
+    assert lib.pnce_workspace_size(F, M, N, 8, 64, 4) < lib.pnce_workspace_size(F, M, N, 8, 64, 2)
+
+
+def test_null_arguments_rejected_without_device(lib):
+    # validation happens before any CUDA call
+    assert lib.pnce_create(None) == 1
+    assert lib.pnce_destroy(None) == 1
+    assert lib.pnce_pilot_destroy(None) == 1
+    assert lib.pnce_estimate(None, None, None, 1, 1, 7, 1, 1, 0, None, 0, None, None) == 1
+    assert lib.pnce_backward(None, None, None, None, 1, 1, 7, 1, 1, None, None, None, 0, None) == 1
