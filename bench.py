@@ -1,0 +1,359 @@
+"""Benchmark: PN-correlation channel estimation throughput on GB300.
+
+One step = the whole estimator on one batch: per-antenna quantisation of the received
+blocks and the tensor-core correlation with its epilogue (pnce_quantize followed by
+pnce_correlate_quantized, the same two kernels pnce_estimate launches), on synthetic
+received blocks shaped like the precision workload (M=128 antennas, N=4095 m-sequence,
+K=16 transmitters x L=128 taps, 512 frames, SNR 0/10/20/30 dB), inputs resident in HBM.
+
+value      CIR taps estimated per second (one tap = one complex H entry), all ranks
+e2e        the same metric through pnce_estimate_host: host (pinned) Y in, host H out
+roofline   the correlation kernel against the measured dense tensor peak for its dtype
+cpu_baseline  the FP64 oracle (Toeplitz product through numpy's BLAS) on a frame sample
+
+Multi-GPU: frames are independent, so every rank estimates its own batch with no
+collective on the data path (weak scaling); NCCL is used for the timing barrier and the
+max over ranks only.  --impl reference times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import channel as C  # noqa: E402
+
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# dense tensor throughput of each operand type relative to bf16 (nominal GB300 figures)
+DTYPE_RATIO = {"fp16": 1.0, "bf16": 1.0, "e4m3": 2.0, "tf32": 0.5}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+def src_hash() -> str:
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2206_05506_gb300", "csrc", "pnce_tc.cu"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_from_profile(workload: str, dtype: str, frames: int):
+    """DRAM bytes per launch of the correlation kernel from the committed ncu summary, or
+    None when there is none for this kernel source / workload."""
+    p = os.path.join(ROOT, "profiles", "tc_corr_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as fh:
+        d = json.load(fh)
+    e = d.get(f"{workload}:{dtype}")
+    if not e or e.get("src_hash") != src_hash():
+        return None
+    # the capture may be of fewer frames: DRAM traffic scales with the frames processed
+    return float(e["bytes_per_frame"]) * frames
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_oracle_sample(bits, Y_sample, K, L, target_s=15.0, max_frames=None):
+    """Time the FP64 oracle on a growing prefix of frames until about target_s of work."""
+    from oracle import pn_oracle as O
+
+    t0 = time.perf_counter()
+    O.estimate(Y_sample[:1], bits, K, L)
+    t1 = time.perf_counter() - t0
+    nf = int(max(1, min(Y_sample.shape[0], (max_frames or 10 ** 9), round(target_s / max(t1, 1e-3)))))
+    t0 = time.perf_counter()
+    H = O.estimate(Y_sample[:nf], bits, K, L)
+    dt = time.perf_counter() - t0
+    return nf, dt, H
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count()
+
+
+def run_reference(args, w):
+    """FP64 CPU oracle as the reference arm: each step estimates a bounded frame sample."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import pn_oracle as O
+
+    nf = args.ref_frames
+    bits, Y = C.make_received(w, frames=nf)
+    for _ in range(args.warmup):
+        O.estimate(Y, bits, w.K, w.L)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.estimate(Y, bits, w.K, w.L)
+    dt = time.perf_counter() - t0
+    taps = nf * w.M * w.K * w.L
+    value = taps * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "CIR taps estimated/s", "value": value, "unit": "taps/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "frames_per_step": nf, "M": w.M, "N": w.N, "K": w.K,
+                   "L": w.L},
+        "cpu_baseline": {"value": value, "unit": "taps/s", "cores": host_cores(),
+                         "kind": "oracle",
+                         "sample": f"{nf} of {w.F} frames per step, FP64 Toeplitz product"},
+        "e2e": {"value": value, "unit": "taps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=C.PRECISION.name, choices=sorted(C.WORKLOADS))
+    ap.add_argument("--dtype", default="fp16", choices=["fp32", "tf32", "fp16", "bf16", "e4m3"])
+    ap.add_argument("--frames", type=int, default=None, help="override frames per step")
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--ref-frames", type=int, default=2, help="frames per reference step")
+    args = ap.parse_args()
+
+    w = C.WORKLOADS[args.workload]
+    if args.frames:
+        w = C.Workload(w.name if args.frames == w.F else f"{w.name}_x{args.frames}", r=w.r,
+                       M=w.M, K=w.K, L=w.L, F=args.frames, snr_db=w.snr_db, seed=w.seed)
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2206_05506_gb300 as pk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- inputs (each rank its own batch: frames offset by rank)
+    bits, Y_host = C.make_received(w, first=rank * w.F if world > 1 else 0)
+    Y_pin = torch.from_numpy(Y_host).pin_memory()
+    Y = Y_pin.to(dev)
+    F, M, N, K, L = w.F, w.M, w.N, w.K, w.L
+    dt = args.dtype
+    pilot = pk.Pilot(bits, device=dev)
+    H = torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    ws = None
+    if dt != "fp32":
+        ws = torch.empty(pk.workspace_size(F, M, N, K, L, dt), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(ev=None):
+        if dt == "fp32":
+            if ev:
+                ev[0].record(stream)
+                ev[1].record(stream)
+            pk.estimate(Y, pilot, K, L, dtype="fp32", out=H)
+            if ev:
+                ev[2].record(stream)
+            return 1
+        if ev:
+            ev[0].record(stream)
+        pk.quantize(Y, dt, workspace=ws)
+        if ev:
+            ev[1].record(stream)
+        pk.correlate_quantized(ws, pilot, F, M, K, L, dt, out=H)
+        if ev:
+            ev[2].record(stream)
+        return 2
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert pk.get_status(dev) == 0
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches = 0
+    for i in range(args.steps):
+        launches += step(evs[i])
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    step_ms = [evs[i][0].elapsed_time(evs[i][2]) for i in range(args.steps)]
+    corr_ms = [evs[i][1].elapsed_time(evs[i][2]) for i in range(args.steps)]
+    quant_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.steps)]
+    total_ms = evs[0][0].elapsed_time(evs[-1][2])
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    assert pk.get_status(dev) == 0
+
+    taps_per_step = F * M * K * L
+    value = taps_per_step * args.steps * world / (total_ms / 1e3)
+
+    # ---- end to end through the host-buffer entry point
+    H_pin = torch.empty((F, M, K, L), dtype=torch.complex64, pin_memory=True)
+    hws = torch.empty(pk.host_workspace_size(F, M, N, K, L, dt), dtype=torch.uint8, device=dev)
+    pk.estimate_host(Y_pin, pilot, K, L, dtype=dt, out=H_pin, workspace=hws)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        pk.lib().pnce_estimate_host(pilot.ctx.handle, pilot.handle, Y_pin.data_ptr(), F, M, N, K,
+                                    L, pk.DTYPES[dt], hws.data_ptr(), hws.numel(),
+                                    H_pin.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_ms = float(t.item())
+    e2e_value = taps_per_step * args.e2e_steps * world / (e2e_ms / 1e3)
+    assert pk.get_status(dev) == 0
+    e2e_matches = bool(torch.equal(H_pin, H.cpu()))
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---- roofline of the correlation kernel
+    peaks, peak_src = load_peaks()
+    flops = 4.0 * F * M * N * K * L          # real GEMM: 2FM rows x N x KL, 2 flop per MAC
+    kern_ms = float(np.mean(corr_ms))
+    if dt == "fp32":
+        roof = None
+    else:
+        long_region = total_ms > 1000.0
+        base = peaks["bf16_tflops_sustained" if long_region else "bf16_tflops"]
+        peak = base * DTYPE_RATIO[dt]
+        achieved = flops / (kern_ms / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic_from_profile(w.name, dt, F),
+                "kernel": "tc_corr_kernel", "peak_source":
+                f"{peak_src} {'sustained' if long_region else 'burst'} bf16 x {DTYPE_RATIO[dt]}"}
+
+    # ---- CPU baseline (FP64 oracle) on a frame sample, plus accuracy of those frames
+    cpu = None
+    nmse = None
+    if not args.no_cpu:
+        from oracle import pn_oracle as O
+        nf, cdt, Href = cpu_oracle_sample(bits, Y_host, K, L)
+        cpu = {"value": nf * M * K * L / cdt, "unit": "taps/s", "cores": host_cores(),
+               "kind": "oracle",
+               "sample": f"first {nf} of {F} frames, FP64 Toeplitz product (numpy BLAS)"}
+        nmse = O.nmse(H[:nf].cpu().numpy(), Href)
+
+    line = {
+        "metric": "CIR taps estimated/s", "value": value, "unit": "taps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dt,
+        "data": "synthetic",
+        "config": {"workload": w.name, "frames": F, "M": M, "N": N, "K": K, "L": L,
+                   "snr_db": list(w.snr_db), "parallelism": f"frames x{world}",
+                   "l2": f"inputs larger than L2 ({Y.numel() * 8 / 1e9:.2f} GB Y per step)"},
+        "breakdown_ms": {"quantize": float(np.mean(quant_ms)), "correlate": kern_ms,
+                         "step_p50": float(np.median(step_ms))},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "taps/s",
+                "h2d_bytes_per_step": int(Y_pin.numel() * 8),
+                "d2h_bytes_per_step": int(H_pin.numel() * 8),
+                "ms_per_step": e2e_ms / args.e2e_steps, "matches_device_result": e2e_matches},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "nmse_vs_oracle": nmse,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

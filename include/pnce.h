@@ -152,10 +152,16 @@ pnce_status pnce_backward(pnce_handle* h, const float* p_dev, const void* Y_dev,
                           size_t workspace_bytes, void* stream);
 
 /*
- * End-to-end estimate from host memory: copies Y_host (complex64 [F][M][N]) to the
- * device, estimates as pnce_estimate, and copies H back to H_host, all enqueued on
- * stream.  The device buffers live in workspace_dev (pnce_host_workspace_size bytes).
- * Frames are processed in chunks so that copies overlap the kernels.
+ * End-to-end estimate from host memory (the paper's frame latency includes the host to
+ * device transfer, Sec. IV-C): copies Y_host (complex64 [F][M][N]) to the device,
+ * estimates as pnce_estimate, and copies H back to H_host (complex64 [F][M][K][L]).
+ * Frames go through in chunks, double buffered, on three streams owned by the handle
+ * (copy-in, kernels, copy-out), so both copy directions overlap the kernels.  The
+ * pipeline starts after the work already queued on `stream`, and `stream` waits for its
+ * end: to the caller the call behaves as if it were enqueued on `stream`.  All device
+ * buffers live in workspace_dev (pnce_host_workspace_size bytes, caller-owned).  Host
+ * buffers should be page-locked for the copies to be asynchronous.  Calls on the same
+ * handle must not overlap in time (they share the handle's pipeline streams).
  */
 size_t pnce_host_workspace_size(int F, int M, int N, int K, int L, int dtype);
 pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const void* Y_host,

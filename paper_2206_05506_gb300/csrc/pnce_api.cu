@@ -75,9 +75,22 @@ pnce_status pnce_create(pnce_handle** out) {
         delete h;
         return PNCE_ENOMEM;
     }
-    if (cudaMemset(h->status_dev, 0, sizeof(int)) != cudaSuccess) {
-        cudaFree(h->status_dev);
-        delete h;
+    bool ok = cudaMemset(h->status_dev, 0, sizeof(int)) == cudaSuccess;
+    const unsigned sf = cudaStreamNonBlocking;
+    ok = ok && cudaStreamCreateWithFlags(&h->s_h2d, sf) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&h->s_comp, sf) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&h->s_d2h, sf) == cudaSuccess;
+    const unsigned ef = cudaEventDisableTiming;
+    for (int i = 0; i < 2 && ok; ++i) {
+        ok = ok && cudaEventCreateWithFlags(&h->ev_in[i], ef) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&h->ev_comp[i], ef) == cudaSuccess;
+        ok = ok && cudaEventCreateWithFlags(&h->ev_out[i], ef) == cudaSuccess;
+    }
+    ok = ok && cudaEventCreateWithFlags(&h->ev_start, ef) == cudaSuccess;
+    for (int i = 0; i < 3 && ok; ++i)
+        ok = ok && cudaEventCreateWithFlags(&h->ev_done[i], ef) == cudaSuccess;
+    if (!ok) {
+        pnce_destroy(h);
         return PNCE_ECUDA;
     }
     *out = h;
@@ -86,7 +99,15 @@ pnce_status pnce_create(pnce_handle** out) {
 
 pnce_status pnce_destroy(pnce_handle* h) {
     if (!h) return PNCE_EINVAL;
-    cudaFree(h->status_dev);
+    for (cudaStream_t s : {h->s_h2d, h->s_comp, h->s_d2h})
+        if (s) cudaStreamDestroy(s);
+    for (int i = 0; i < 2; ++i)
+        for (cudaEvent_t e : {h->ev_in[i], h->ev_comp[i], h->ev_out[i]})
+            if (e) cudaEventDestroy(e);
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
+    for (int i = 0; i < 3; ++i)
+        if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
+    if (h->status_dev) cudaFree(h->status_dev);
     delete h;
     return PNCE_OK;
 }
@@ -246,17 +267,120 @@ pnce_status pnce_backward(pnce_handle* h, const float* p_dev, const void* Y_dev,
         workspace_bytes, static_cast<cudaStream_t>(stream)));
 }
 
+namespace {
+
+// Host pipeline layout: frames go through in chunks of fc frames, two slots of
+// (Y chunk, H chunk) so that copy-in of chunk i+1 and copy-out of chunk i-1 overlap the
+// kernels of chunk i, plus the quantisation workspace of one chunk.
+struct HostLayout {
+    int fc;                        // frames per chunk
+    size_t y_bytes, h_bytes;       // per slot
+    size_t y_off[2], h_off[2], q_off, total;
+};
+
+HostLayout host_layout(int F, int M, int N, int K, int L, int dtype) {
+    HostLayout l{};
+    const size_t frame_y = (size_t)M * N * 8;
+    const size_t target = (size_t)128 << 20;       // ~128 MB of Y per chunk
+    long long fc = (long long)((target + frame_y - 1) / frame_y);
+    const long long min_chunks = 4;                // enough chunks to overlap copy and compute
+    if ((F + fc - 1) / fc < min_chunks) fc = (F + min_chunks - 1) / min_chunks;
+    if (fc < 1) fc = 1;
+    if (fc > F) fc = F;
+    l.fc = (int)fc;
+    l.y_bytes = pnce::round_up((size_t)fc * frame_y, 256);
+    l.h_bytes = pnce::round_up((size_t)fc * M * (size_t)K * L * 8, 256);
+    size_t off = 0;
+    for (int b = 0; b < 2; ++b) {
+        l.y_off[b] = off;
+        off += l.y_bytes;
+        l.h_off[b] = off;
+        off += l.h_bytes;
+    }
+    l.q_off = off;
+    if (dtype != PNCE_FP32_SIMT) off += pnce::quant_layout((long long)fc * M, N, dtype).total;
+    l.total = off;
+    return l;
+}
+
+}  // namespace
+
 size_t pnce_host_workspace_size(int F, int M, int N, int K, int L, int dtype) {
-    (void)F; (void)M; (void)N; (void)K; (void)L; (void)dtype;
-    return 0;
+    if (!shape_ok(F, M, N, K, L)) return 0;
+    if (dtype != PNCE_FP32_SIMT && !is_tc(dtype)) return 0;
+    return host_layout(F, M, N, K, L, dtype).total;
 }
 
 pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const void* Y_host, int F,
                                int M, int N, int K, int L, int dtype, void* workspace_dev,
                                size_t workspace_bytes, void* H_host, void* stream) {
-    (void)h; (void)pilot; (void)Y_host; (void)F; (void)M; (void)N; (void)K; (void)L;
-    (void)dtype; (void)workspace_dev; (void)workspace_bytes; (void)H_host; (void)stream;
-    return PNCE_EUNSUPPORTED;
+    if (!h || !pilot || !Y_host || !H_host || !workspace_dev) return PNCE_EINVAL;
+    if (!shape_ok(F, M, N, K, L)) return PNCE_EINVAL;
+    if (dtype != PNCE_FP32_SIMT && !is_tc(dtype)) return PNCE_EINVAL;
+    if (!aligned16(workspace_dev)) return PNCE_EINVAL;
+    const HostLayout lay = host_layout(F, M, N, K, L, dtype);
+    if (workspace_bytes < lay.total) return PNCE_EINVAL;
+    pnce_status st = check_device(h);
+    if (st != PNCE_OK) return st;
+    if (pilot->device != h->device || pilot->N != N) return PNCE_ESTATE;
+    if (dtype != PNCE_FP32_SIMT && !(h->cc_major == 10 && h->cc_minor == 3))
+        return PNCE_EUNSUPPORTED;
+
+    cudaStream_t user = static_cast<cudaStream_t>(stream);
+    unsigned char* ws = static_cast<unsigned char*>(workspace_dev);
+    const unsigned char* yh = static_cast<const unsigned char*>(Y_host);
+    unsigned char* hh = static_cast<unsigned char*>(H_host);
+    const size_t frame_y = (size_t)M * N * 8, frame_h = (size_t)M * K * L * 8;
+
+    // the pipeline starts after the work already queued on the caller's stream
+    if (cudaEventRecord(h->ev_start, user) != cudaSuccess) return PNCE_ECUDA;
+    for (cudaStream_t s : {h->s_h2d, h->s_comp, h->s_d2h})
+        if (cudaStreamWaitEvent(s, h->ev_start, 0) != cudaSuccess) return PNCE_ECUDA;
+
+    for (int f0 = 0, i = 0; f0 < F; f0 += lay.fc, ++i) {
+        const int b = i & 1;
+        const int fc = (F - f0 < lay.fc) ? (F - f0) : lay.fc;
+        void* yd = ws + lay.y_off[b];
+        void* hd = ws + lay.h_off[b];
+        // copy-in: slot b is free once the kernels of chunk i-2 have read it
+        if (i >= 2 && cudaStreamWaitEvent(h->s_h2d, h->ev_comp[b], 0) != cudaSuccess)
+            return PNCE_ECUDA;
+        if (cudaMemcpyAsync(yd, yh + (size_t)f0 * frame_y, (size_t)fc * frame_y,
+                            cudaMemcpyHostToDevice, h->s_h2d) != cudaSuccess ||
+            cudaEventRecord(h->ev_in[b], h->s_h2d) != cudaSuccess)
+            return PNCE_ECUDA;
+        // kernels: need the input, and H slot b drained by the copy-out of chunk i-2
+        if (cudaStreamWaitEvent(h->s_comp, h->ev_in[b], 0) != cudaSuccess) return PNCE_ECUDA;
+        if (i >= 2 && cudaStreamWaitEvent(h->s_comp, h->ev_out[b], 0) != cudaSuccess)
+            return PNCE_ECUDA;
+        const long long A = (long long)fc * M;
+        if (dtype == PNCE_FP32_SIMT) {
+            st = from_cuda(pnce::launch_simt_bits(pilot, static_cast<const float2*>(yd), A, N,
+                                                  K * L, static_cast<float2*>(hd), h->s_comp));
+        } else {
+            st = from_cuda(pnce::launch_quantize(static_cast<const float2*>(yd), A, N, dtype,
+                                                 ws + lay.q_off, nullptr, nullptr, h->s_comp));
+            if (st == PNCE_OK)
+                st = pnce::launch_tc(h, pilot, A, N, K * L, dtype, ws + lay.q_off,
+                                     static_cast<float2*>(hd), h->s_comp);
+        }
+        if (st != PNCE_OK) return st;
+        if (cudaEventRecord(h->ev_comp[b], h->s_comp) != cudaSuccess) return PNCE_ECUDA;
+        // copy-out
+        if (cudaStreamWaitEvent(h->s_d2h, h->ev_comp[b], 0) != cudaSuccess ||
+            cudaMemcpyAsync(hh + (size_t)f0 * frame_h, hd, (size_t)fc * frame_h,
+                            cudaMemcpyDeviceToHost, h->s_d2h) != cudaSuccess ||
+            cudaEventRecord(h->ev_out[b], h->s_d2h) != cudaSuccess)
+            return PNCE_ECUDA;
+    }
+    // the caller's stream resumes when all three pipeline streams are done
+    cudaStream_t ss[3] = {h->s_h2d, h->s_comp, h->s_d2h};
+    for (int k = 0; k < 3; ++k) {
+        if (cudaEventRecord(h->ev_done[k], ss[k]) != cudaSuccess ||
+            cudaStreamWaitEvent(user, h->ev_done[k], 0) != cudaSuccess)
+            return PNCE_ECUDA;
+    }
+    return PNCE_OK;
 }
 
 }  // extern "C"

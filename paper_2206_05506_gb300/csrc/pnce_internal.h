@@ -13,6 +13,10 @@ struct pnce_handle {
     int max_smem_optin;
     int cc_major, cc_minor;
     int* status_dev;                    // latched device-side status word
+    // host-buffer pipeline (pnce_estimate_host): copy-in, compute and copy-out streams,
+    // and per double-buffer slot events
+    cudaStream_t s_h2d, s_comp, s_d2h;
+    cudaEvent_t ev_in[2], ev_comp[2], ev_out[2], ev_start, ev_done[3];
 };
 
 struct pnce_pilot {

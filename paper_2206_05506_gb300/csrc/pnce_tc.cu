@@ -10,9 +10,12 @@
 //    (column 8q + r, sample n0 + EPR*t + c) is p[(s + G*(QS*q + TS*t) + r + c) mod N].
 //    Every 8-row x 16-byte core matrix of the canonical no-swizzle K-major layout is then
 //    one of a short list indexed by D = QS*q + TS*t, so the pilot operand of a stage is
-//    that list alone (<= 70 core matrices, <= 9 KB), generated from the packed pilot bits
-//    by one warp, and the shared-memory descriptor's two core-matrix strides (LBO along K,
-//    SBO along the lags) point into it with overlap.
+//    that list alone, and the shared-memory descriptor's two core-matrix strides (LBO
+//    along K, SBO along the lags) point into it with overlap.  Successive K blocks of one
+//    lag block only shift along that list, so when it fits, the whole list for every K
+//    block of the CTA's lag block (N/8 + BN/8 core matrices for 16-bit types, ~70 KB at
+//    N = 4095) is generated once at kernel start and stays resident ("resident pilot");
+//    otherwise one warp regenerates each stage's list (<= 70 core matrices, <= 9 KB).
 // Epilogue: tcgen05.ld of 32 accumulator columns, re/im pairing by lane shuffles (rows 2a,
 //    2a+1 are adjacent TMEM lanes), the per-antenna factor 2^-s_a / N, lag order restored,
 //    staged through a bank-conflict-free swizzled buffer and written as whole 256-byte
@@ -31,6 +34,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <mutex>
 
 #include "pnce_internal.h"
@@ -39,7 +43,8 @@ namespace {
 
 constexpr int THREADS = 256;
 constexpr int BM = 128;                   // accumulator rows (TMEM lanes) per tile
-constexpr int STAGES = 8;
+constexpr int STAGES = 8;                 // maximum pipeline depth
+constexpr int MIN_RES_STAGES = 4;         // fewest stages worth keeping the pilot resident
 constexpr int A_STAGE = BM * 128;         // 16 KB
 constexpr int ACC_COLS = 256;
 constexpr int TMEM_COLS = 512;
@@ -54,6 +59,9 @@ struct TcParams {
     int num_jt;             // lag blocks
     long long num_tiles;
     int num_kb;             // pipeline stages per tile (K blocks)
+    int stages;             // pipeline depth (<= STAGES)
+    int b_region;           // bytes of the pilot operand region
+    int res_rows;           // resident pilot: 16-byte rows to generate (0 otherwise)
     unsigned long long wait_limit_ns;
     int* err;
 };
@@ -96,11 +104,7 @@ struct Ctl {
     int abort_flag;
 };
 
-template <int DT>
-constexpr size_t smem_bytes() {
-    return 1024 /* alignment slack */ + (size_t)STAGES * A_STAGE +
-           (size_t)STAGES * b_stage_bytes<DT>() + EPI_BYTES + sizeof(Ctl);
-}
+constexpr size_t smem_fixed() { return 1024 /* alignment slack */ + EPI_BYTES + sizeof(Ctl); }
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -256,18 +260,20 @@ __device__ __forceinline__ uint4 pilot_row(uint32_t x) {
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
-// Pilot operand of one stage: core matrix D, row r (byte offset 128 D + 16 r) holds the
-// EPR pilot values starting at sequence index s_start + G*D + r (mod N).
+// Pilot operand: core matrix D, row r (byte offset 128 D + 16 r) holds the EPR pilot
+// values starting at sequence index s_start + G*D + r (mod N).  Rows idx = 8 D + r are
+// shared out over nthr threads (a multiple of 8), thread `tid` taking tid, tid+nthr, ...
 template <int DT>
-__device__ __forceinline__ void gen_pilot_stage(unsigned char* dst, const uint32_t* __restrict__ ext,
-                                                int N, long long s_start, int rows, int lane) {
+__device__ __forceinline__ void gen_pilot_rows(unsigned char* dst, const uint32_t* __restrict__ ext,
+                                               int N, long long s_start, int rows, int tid,
+                                               int nthr) {
     using F = TcFmt<DT>;
-    // row index idx = 8 D + r: sequence offset G*(idx >> 3) + (idx & 7); lanes step by 32
-    // rows, i.e. by 4 core matrices = 4 G sequence positions
-    long long w0 = s_start + (long long)F::G * (lane >> 3) + (lane & 7);
+    // row idx has sequence offset G*(idx >> 3) + (idx & 7); a step of nthr rows is a
+    // step of nthr/8 core matrices
+    long long w0 = s_start + (long long)F::G * (tid >> 3) + (tid & 7);
     int pos = (int)(((w0 % N) + N) % N);
-    constexpr int step = 4 * F::G;
-    for (int idx = lane; idx < rows; idx += 32) {
+    const int step = (int)(((long long)F::G * (nthr >> 3)) % N);
+    for (int idx = tid; idx < rows; idx += nthr) {
         const uint32_t lo = __ldg(ext + (pos >> 5)), hi = __ldg(ext + (pos >> 5) + 1);
         const uint64_t win = (((uint64_t)hi << 32) | lo) >> (pos & 31);
         const uint4 v = pilot_row<DT>((uint32_t)win);
@@ -279,7 +285,7 @@ __device__ __forceinline__ void gen_pilot_stage(unsigned char* dst, const uint32
 
 // ------------------------------------------------------------------- the kernel
 
-template <int DT>
+template <int DT, bool RES>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
                const float* __restrict__ row_scale, float2* __restrict__ H, const TcParams prm) {
@@ -292,16 +298,17 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     extern __shared__ unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int nst = prm.stages;
     unsigned char* sA = base;
-    unsigned char* sB = sA + STAGES * A_STAGE;
-    float4* sEpi = reinterpret_cast<float4*>(sB + STAGES * BSTAGE);
+    unsigned char* sB = sA + nst * A_STAGE;
+    float4* sEpi = reinterpret_cast<float4*>(sB + prm.b_region);
     Ctl* ctl = reinterpret_cast<Ctl*>(reinterpret_cast<unsigned char*>(sEpi) + EPI_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int BN = prm.BN, num_jt = prm.num_jt, num_kb = prm.num_kb;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < nst; ++s) {
             mbar_init(&ctl->full_a[s], 1);
             mbar_init(&ctl->full_b[s], 1);
             mbar_init(&ctl->empty[s], 1);
@@ -317,6 +324,13 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     if (warp == 0 && lane == 0) {
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
                      : "memory");
+    }
+    if constexpr (RES) {
+        // the CTA's lag block never changes (grid is a multiple of num_jt): build the
+        // pilot operand of all its K blocks once
+        const long long j0 = (long long)(blockIdx.x % num_jt) * BN;
+        gen_pilot_rows<DT>(sB, ext, prm.N, -j0 - BN + 1, prm.res_rows, threadIdx.x, THREADS);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -346,15 +360,15 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                     mbar_arrive_tx(&ctl->full_a[stage], A_STAGE);
                     tma_load_2d(sA + stage * A_STAGE, &tmap, kb * F::BK, y, &ctl->full_a[stage]);
                     ++issued;
-                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
                 }
             }
             // drain: the last loads issued must have landed before the CTA may exit
-            const long long first = issued > STAGES ? issued - STAGES : 0;
+            const long long first = issued > nst ? issued - nst : 0;
             for (long long i = first; i < issued; ++i)
-                wait_bar(&ctl->full_a[i % STAGES], (uint32_t)((i / STAGES) & 1), ctl, prm, false);
+                wait_bar(&ctl->full_a[i % nst], (uint32_t)((i / nst) & 1), ctl, prm, false);
         }
-    } else if (warp == 1) {
+    } else if (warp == 1 && !RES) {
         // ---------------------------------------------------- pilot operand generator
         const int rows = ncm<DT>(BN) * 8;
         uint32_t stage = 0, phase = 0;
@@ -367,11 +381,11 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) { ok = false; break; }
                 const long long s_start = (long long)kb * F::BK - j0 - BN + 1;
-                gen_pilot_stage<DT>(sB + stage * BSTAGE, ext, prm.N, s_start, rows, lane);
+                gen_pilot_rows<DT>(sB + stage * BSTAGE, ext, prm.N, s_start, rows, lane, 32);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&ctl->full_b[stage]);
-                if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
             }
         }
     } else if (warp == 2) {
@@ -389,13 +403,16 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                 const uint32_t d = tmem + acc * ACC_COLS;
                 for (int kb = 0; kb < num_kb; ++kb) {
                     if (!wait_bar(&ctl->full_a[stage], phase, ctl, prm, true) ||
-                        !wait_bar(&ctl->full_b[stage], phase, ctl, prm, true)) {
+                        (!RES && !wait_bar(&ctl->full_b[stage], phase, ctl, prm, true))) {
                         ok = false;
                         break;
                     }
                     fence_after();
                     const uint32_t a0 = su32(sA + stage * A_STAGE);
-                    const uint32_t b0 = su32(sB + stage * BSTAGE);
+                    // resident: K block kb starts BK/EPR core matrices (times TS) further on
+                    const uint32_t b0 =
+                        RES ? su32(sB) + 128u * F::TS * (uint32_t)(kb * (F::BK / F::EPR))
+                            : su32(sB + stage * BSTAGE);
 #pragma unroll
                     for (int ks = 0; ks < KSTEPS; ++ks) {
                         const uint64_t ad = sdesc(a0 + 32u * ks, 16u, 1024u, 2u);
@@ -405,7 +422,7 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                     umma_commit(&ctl->empty[stage]);
                     last_bar = &ctl->empty[stage];
                     last_par = phase;
-                    if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
                 }
                 if (!ok) break;
                 umma_commit(&ctl->tfull[acc]);
@@ -566,12 +583,32 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     if (grid > prm.num_tiles) grid = prm.num_tiles;
     if (grid < 1) return PNCE_OK;
 
-    const size_t smem = smem_bytes<DT>();
-    if ((int)smem > h->max_smem_optin) return PNCE_EUNSUPPORTED;
-    if (cudaFuncSetAttribute(tc_corr_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
+    // resident pilot operand when every CTA keeps one lag block and the list fits beside
+    // at least MIN_RES_STAGES pipeline stages
+    const long long avail = (long long)h->max_smem_optin - (long long)smem_fixed();
+    const long long res_cm = (long long)(prm.BN / 8 - 1) * F::QS +
+                             ((long long)prm.num_kb * (F::BK / F::EPR) - 1) * F::TS + 1;
+    const long long res_bytes = (res_cm * 128 + 1023) / 1024 * 1024;
+    // PNCE_TC_STAGED_PILOT=1 forces the per-stage pilot path (used to test both paths)
+    const char* force = getenv("PNCE_TC_STAGED_PILOT");
+    const bool res = !(force && force[0] == '1') && (grid % prm.num_jt == 0) &&
+                     (avail - res_bytes) / A_STAGE >= MIN_RES_STAGES;
+    if (res) {
+        prm.stages = (int)std::min<long long>(STAGES, (avail - res_bytes) / A_STAGE);
+        prm.b_region = (int)res_bytes;
+        prm.res_rows = (int)(res_cm * 8);
+    } else {
+        prm.stages = STAGES;
+        prm.b_region = STAGES * b_stage_bytes<DT>();
+        prm.res_rows = 0;
+    }
+    const size_t smem = smem_fixed() + (size_t)prm.stages * A_STAGE + prm.b_region;
+    if ((long long)smem > h->max_smem_optin) return PNCE_EUNSUPPORTED;
+    auto kern = res ? tc_corr_kernel<DT, true> : tc_corr_kernel<DT, false>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
         return PNCE_ECUDA;
-    tc_corr_kernel<DT><<<(unsigned)grid, THREADS, smem, s>>>(
+    kern<<<(unsigned)grid, THREADS, smem, s>>>(
         map, pilot->ext_bits_dev, reinterpret_cast<const float*>(wsb + lay.scale_offset), H, prm);
     return cudaGetLastError() == cudaSuccess ? PNCE_OK : PNCE_ECUDA;
 }

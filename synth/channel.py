@@ -126,6 +126,20 @@ DIFFERENTIATION = Workload("n1023_m64_k8_l64_f64", r=10, M=64, K=8, L=64, F=64,
 WORKLOADS = {w.name: w for w in (SMALL, PAPER_SCALE, PRECISION, DIFFERENTIATION)}
 
 
+def make_received(w: Workload, frames: int | None = None, first: int = 0):
+    """(bits, Y) for frames [first, first + frames) of workload w, without keeping h."""
+    F = w.F if frames is None else frames
+    bits = mseq.mseq_bits(w.r, w.seed)
+    snr = w.frame_snr()
+    Y = np.empty((F, w.M, w.N), dtype=np.complex64)
+    for i in range(F):
+        f = first + i
+        rng = np.random.default_rng([w.seed, f])
+        h = channel(rng, 1, w.M, w.K, w.L)
+        Y[i] = received(h, bits, snr[f % snr.size], rng)[0]
+    return bits, Y
+
+
 def make(w: Workload, frames: int | None = None, noise: bool = True):
     """(bits, h, Y) for workload w, optionally only its first `frames` frames.
 

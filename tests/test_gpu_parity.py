@@ -109,13 +109,26 @@ def test_quantizer_bit_exact(pk, shape, dtype):
     Q, se = O.quantize(Y, dtype)
     N = Y.shape[2]
     got = _decode(res["q"], dtype)[:, :N].reshape(F * M, 2, N)
-    want = np.stack([Q.real, Q.imag], axis=1).reshape(F * M, 2, N)
+    want = np.stack([Q.real, Q.imag], axis=-2).reshape(F * M, 2, N)
     assert np.array_equal(got, want)
     assert np.array_equal(res["exps"].cpu().numpy(), se.reshape(-1))
     fac = np.float32(1.0 / N) * np.ldexp(np.float32(1.0), -se.reshape(-1)).astype(np.float32)
     assert np.array_equal(res["factor"].cpu().numpy(), fac)
     pw = (np.abs(Y.astype(np.complex128)) ** 2).mean(axis=-1).reshape(-1)
     assert np.allclose(res["power"].cpu().numpy(), pw, rtol=1e-12, atol=0)
+
+
+def test_tensor_core_staged_pilot_path(pk, monkeypatch):
+    # the per-stage pilot generator (used when the resident list does not fit) on shapes
+    # with several K blocks, lag tiles and a ragged row tile
+    monkeypatch.setenv("PNCE_TC_STAGED_PILOT", "1")
+    for shape in [(10, 100, 5, 60, 3), (12, 64, 16, 128, 2), (6, 3, 7, 9, 2)]:
+        r, M, K, L, F = shape
+        bits, _, Y = _case(*shape, seed=11)
+        for dtype in TC:
+            H = _run(pk, Y, bits, K, L, dtype)
+            refq = O.estimate_quantized(Y, bits, K, L, dtype)
+            assert O.nmse(H, refq) <= TOL_Q[dtype], (shape, dtype)
 
 
 @pytest.mark.parametrize("dtype", ["fp32"] + TC)
