@@ -128,27 +128,36 @@ pnce_status pnce_correlate_quantized(pnce_handle* h, const pnce_pilot* pilot,
                                      const void* workspace_dev, size_t workspace_bytes,
                                      void* H_dev, void* stream);
 
+/* How pnce_estimate_real_pilot / pnce_backward read their float pilot argument. */
+typedef enum {
+    PNCE_PILOT_REAL = 0,    /* the argument is the pilot p itself */
+    PNCE_PILOT_TANH = 1     /* the argument is theta and the pilot is p = tanh(theta) */
+} pnce_pilot_map;
+
 /*
- * Estimate with a real-valued pilot p_dev (float32 [N]) in place of the +-1 sequence:
- * H = (1/N) sum_n Y[n] p[(n - j) mod N], FP32 on the CUDA cores.  This is the forward
- * of the relaxed pilot p = tanh(theta) used for pilot optimisation.
+ * Estimate with a real-valued pilot (float32 [N], device) in place of the +-1 sequence:
+ * H = (1/N) sum_n Y[n] p[(n - j) mod N], FP32 on the CUDA cores.  With PNCE_PILOT_TANH
+ * the argument is theta and p = tanh(theta) is formed inside the kernel: the forward of
+ * the relaxed pilot used for end-to-end pilot optimisation.
  */
-pnce_status pnce_estimate_real_pilot(pnce_handle* h, const float* p_dev, const void* Y_dev,
-                                     int F, int M, int N, int K, int L, void* H_dev,
-                                     void* stream);
+pnce_status pnce_estimate_real_pilot(pnce_handle* h, const float* pilot_dev, int pilot_map,
+                                     const void* Y_dev, int F, int M, int N, int K, int L,
+                                     void* H_dev, void* stream);
 
 /*
  * Adjoint of pnce_estimate_real_pilot for a real loss.  G_dev = dLoss/dRe(H) +
  * i dLoss/dIm(H), complex64 [F][M][K][L].  Outputs (either may be NULL to skip):
  *   dY_dev[f][m][n] = (1/N) sum_{j<KL} G[f][m][j] p[(n - j) mod N]      complex64
- *   dp_dev[q]       = (1/N) sum_{f,m,j} Re(conj(G[f][m][j]) Y[f][m][(q + j) mod N])
- * dp is reduced deterministically in two stages through workspace_dev
- * (pnce_backward_workspace_size bytes).
+ *   dpilot_dev[q]   = (1/N) sum_{f,m,j} Re(conj(G[f][m][j]) Y[f][m][(q + j) mod N])
+ * and with PNCE_PILOT_TANH, dpilot_dev is the gradient with respect to theta,
+ * dp[q] * (1 - tanh(theta[q])^2).  The pilot sum is reduced deterministically in two
+ * stages through workspace_dev (pnce_backward_workspace_size bytes), so repeated calls
+ * give identical bits.
  */
 size_t pnce_backward_workspace_size(int F, int M, int N, int K, int L);
-pnce_status pnce_backward(pnce_handle* h, const float* p_dev, const void* Y_dev,
-                          const void* G_dev, int F, int M, int N, int K, int L,
-                          void* dY_dev, float* dp_dev, void* workspace_dev,
+pnce_status pnce_backward(pnce_handle* h, const float* pilot_dev, int pilot_map,
+                          const void* Y_dev, const void* G_dev, int F, int M, int N, int K,
+                          int L, void* dY_dev, float* dpilot_dev, void* workspace_dev,
                           size_t workspace_bytes, void* stream);
 
 /*

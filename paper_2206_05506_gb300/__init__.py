@@ -26,7 +26,7 @@ from . import _lib
 from ._lib import DTYPES, PnceError, check
 
 __all__ = ["Pilot", "Context", "estimate", "quantize", "correlate_quantized",
-           "estimate_real_pilot", "backward", "estimate_host", "workspace_size",
+           "estimate_real_pilot", "backward", "estimate_host", "PILOT_MAPS", "workspace_size",
            "host_workspace_size", "backward_workspace_size", "get_status", "DTYPES",
            "PnceError", "lib"]
 
@@ -233,23 +233,34 @@ def correlate_quantized(workspace: torch.Tensor, pilot: Pilot, F, M, K, L, dtype
     return H
 
 
-def estimate_real_pilot(Y: torch.Tensor, p: torch.Tensor, K: int, L: int, out=None):
-    """FP32 estimate with a real-valued pilot p (float32 CUDA tensor [N])."""
+PILOT_MAPS = {"real": 0, "tanh": 1}
+
+
+def estimate_real_pilot(Y: torch.Tensor, p: torch.Tensor, K: int, L: int, out=None,
+                        pilot_map: str = "real"):
+    """FP32 estimate with a real-valued pilot (float32 CUDA tensor [N]).
+
+    pilot_map="tanh": p holds theta and the pilot is tanh(theta), formed in the kernel.
+    """
     F, M, N = _check_y(Y)
     if p.dtype != torch.float32 or p.shape != (N,) or not p.is_contiguous() or p.device != Y.device:
         raise ValueError("p must be a contiguous float32 tensor [N] on Y's device")
     dev = Y.device
     H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
     with torch.cuda.device(dev):
-        check(lib().pnce_estimate_real_pilot(context(dev).handle, p.data_ptr(), Y.data_ptr(), F,
-                                             M, N, K, L, H.data_ptr(), _stream(dev)),
+        check(lib().pnce_estimate_real_pilot(context(dev).handle, p.data_ptr(),
+                                             PILOT_MAPS[pilot_map], Y.data_ptr(), F, M, N, K, L,
+                                             H.data_ptr(), _stream(dev)),
               "pnce_estimate_real_pilot")
     return H
 
 
 def backward(p: torch.Tensor, Y: torch.Tensor, G: torch.Tensor, K: int, L: int,
-             need_dY=True, need_dp=True):
-    """Adjoint of estimate_real_pilot: (dY [F, M, N] complex64, dp [N] float32)."""
+             need_dY=True, need_dp=True, pilot_map: str = "real"):
+    """Adjoint of estimate_real_pilot: (dY [F, M, N] complex64, dpilot [N] float32).
+
+    With pilot_map="tanh" the second output is the gradient with respect to theta.
+    """
     F, M, N = _check_y(Y)
     if G.dtype != torch.complex64 or tuple(G.shape) != (F, M, K, L) or not G.is_contiguous():
         raise ValueError("G must be a contiguous complex64 tensor [F, M, K, L]")
@@ -259,9 +270,9 @@ def backward(p: torch.Tensor, Y: torch.Tensor, G: torch.Tensor, K: int, L: int,
     need = backward_workspace_size(F, M, N, K, L) if need_dp else 0
     ws = _workspace(dev, need, key="bwd")
     with torch.cuda.device(dev):
-        check(lib().pnce_backward(context(dev).handle, p.data_ptr(), Y.data_ptr(), G.data_ptr(),
-                                  F, M, N, K, L, _ptr(dY), _ptr(dp), _ptr(ws),
-                                  0 if ws is None else ws.numel(), _stream(dev)),
+        check(lib().pnce_backward(context(dev).handle, p.data_ptr(), PILOT_MAPS[pilot_map],
+                                  Y.data_ptr(), G.data_ptr(), F, M, N, K, L, _ptr(dY), _ptr(dp),
+                                  _ptr(ws), 0 if ws is None else ws.numel(), _stream(dev)),
               "pnce_backward")
     return dY, dp
 

@@ -37,9 +37,9 @@ _SIGS = {
     "pnce_estimate": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
     "pnce_quantize": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp, _vp, _vp]),
     "pnce_correlate_quantized": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
-    "pnce_estimate_real_pilot": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp]),
+    "pnce_estimate_real_pilot": (_i, [_vp, _vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp]),
     "pnce_backward_workspace_size": (_sz, [_i, _i, _i, _i, _i]),
-    "pnce_backward": (_i, [_vp, _vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
+    "pnce_backward": (_i, [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
     "pnce_host_workspace_size": (_sz, [_i, _i, _i, _i, _i, _i]),
     "pnce_estimate_host": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
 }

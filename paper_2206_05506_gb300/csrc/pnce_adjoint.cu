@@ -4,6 +4,7 @@
 // G = dLoss/dRe(H) + i dLoss/dIm(H):
 //   dY[a][n] = (1/N) sum_j G[a][j] p[(n - j) mod N]       (pnce_simt.cu, pilot reversed)
 //   dp[q]    = (1/N) sum_a sum_j Re(conj(G[a][j]) Y[a][(q + j) mod N])   (this file)
+// and, when the pilot is p = tanh(theta), dtheta[q] = dp[q] (1 - tanh(theta[q])^2).
 //
 // dp: block = 8 warps over one tile of 256 consecutive q (8 per lane); each warp takes
 // antennas warp, warp+8, ... of the block's antenna group and, per 128-lag chunk, stages
@@ -99,21 +100,25 @@ dp_partial_kernel(const float2* __restrict__ G, const float2* __restrict__ Y, lo
     }
 }
 
+// dp[q] = invN * sum_g partial[g][q], or, for the tanh map, that times 1 - tanh(theta)^2
 __global__ void dp_final_kernel(const float* __restrict__ partial, long long groups, int N,
-                                int pitch, float invN, float* __restrict__ dp) {
+                                int pitch, float invN, const float* __restrict__ theta,
+                                float* __restrict__ dp) {
     const int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= N) return;
     float s = 0.f;
     for (long long g = 0; g < groups; ++g) s += partial[g * (long long)pitch + q];
-    dp[q] = s * invN;
+    s *= invN;
+    if (theta) {
+        const float t = tanhf(theta[q]);
+        s *= (1.0f - t * t);
+    }
+    dp[q] = s;
 }
 
 }  // namespace
 
 namespace pnce {
-
-cudaError_t launch_adjoint_dy(const float* p, const float2* G, long long A, int N, int KL,
-                              float2* dY, cudaStream_t s);
 
 size_t backward_workspace(long long A, int N, int KL) {
     (void)KL;
@@ -121,11 +126,11 @@ size_t backward_workspace(long long A, int N, int KL) {
     return round_up((size_t)groups * (size_t)round_up((size_t)N, 64) * sizeof(float), 256);
 }
 
-cudaError_t launch_backward(const float* p, const float2* Y, const float2* G, long long A, int N,
-                            int KL, float2* dY, float* dp, void* ws, size_t ws_bytes,
-                            cudaStream_t s) {
+cudaError_t launch_backward(const float* p, bool tanh_map, const float2* Y, const float2* G,
+                            long long A, int N, int KL, float2* dY, float* dp, void* ws,
+                            size_t ws_bytes, cudaStream_t s) {
     if (dY) {
-        cudaError_t e = launch_adjoint_dy(p, G, A, N, KL, dY, s);
+        cudaError_t e = launch_adjoint_dy(p, tanh_map, G, A, N, KL, dY, s);
         if (e != cudaSuccess) return e;
     }
     if (dp) {
@@ -140,7 +145,8 @@ cudaError_t launch_backward(const float* p, const float2* Y, const float2* G, lo
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         dp_final_kernel<<<(N + 255) / 256, 256, 0, s>>>(partial, groups, N, pitch,
-                                                        (float)(1.0 / (double)N), dp);
+                                                        (float)(1.0 / (double)N),
+                                                        tanh_map ? p : nullptr, dp);
         return cudaGetLastError();
     }
     return cudaSuccess;

@@ -228,14 +228,17 @@ pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y
                            static_cast<float2*>(H_dev), s);
 }
 
-pnce_status pnce_estimate_real_pilot(pnce_handle* h, const float* p_dev, const void* Y_dev, int F,
-                                     int M, int N, int K, int L, void* H_dev, void* stream) {
+pnce_status pnce_estimate_real_pilot(pnce_handle* h, const float* p_dev, int pilot_map,
+                                     const void* Y_dev, int F, int M, int N, int K, int L,
+                                     void* H_dev, void* stream) {
     if (!h || !p_dev || !Y_dev || !H_dev) return PNCE_EINVAL;
+    if (pilot_map != PNCE_PILOT_REAL && pilot_map != PNCE_PILOT_TANH) return PNCE_EINVAL;
     if (!shape_ok(F, M, N, K, L)) return PNCE_EINVAL;
     if (!aligned16(Y_dev) || !aligned16(H_dev) || !aligned16(p_dev)) return PNCE_EINVAL;
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
-    return from_cuda(pnce::launch_simt_real(p_dev, static_cast<const float2*>(Y_dev),
+    return from_cuda(pnce::launch_simt_real(p_dev, pilot_map == PNCE_PILOT_TANH,
+                                            static_cast<const float2*>(Y_dev),
                                             (long long)F * M, N, K * L,
                                             static_cast<float2*>(H_dev),
                                             static_cast<cudaStream_t>(stream)));
@@ -246,10 +249,12 @@ size_t pnce_backward_workspace_size(int F, int M, int N, int K, int L) {
     return pnce::backward_workspace((long long)F * M, N, K * L);
 }
 
-pnce_status pnce_backward(pnce_handle* h, const float* p_dev, const void* Y_dev, const void* G_dev,
-                          int F, int M, int N, int K, int L, void* dY_dev, float* dp_dev,
-                          void* workspace_dev, size_t workspace_bytes, void* stream) {
+pnce_status pnce_backward(pnce_handle* h, const float* p_dev, int pilot_map, const void* Y_dev,
+                          const void* G_dev, int F, int M, int N, int K, int L, void* dY_dev,
+                          float* dp_dev, void* workspace_dev, size_t workspace_bytes,
+                          void* stream) {
     if (!h || !p_dev || !G_dev) return PNCE_EINVAL;
+    if (pilot_map != PNCE_PILOT_REAL && pilot_map != PNCE_PILOT_TANH) return PNCE_EINVAL;
     if (!shape_ok(F, M, N, K, L)) return PNCE_EINVAL;
     if (!aligned16(p_dev) || !aligned16(G_dev)) return PNCE_EINVAL;
     if (dY_dev && !aligned16(dY_dev)) return PNCE_EINVAL;
@@ -262,7 +267,8 @@ pnce_status pnce_backward(pnce_handle* h, const float* p_dev, const void* Y_dev,
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
     return from_cuda(pnce::launch_backward(
-        p_dev, static_cast<const float2*>(Y_dev), static_cast<const float2*>(G_dev),
+        p_dev, pilot_map == PNCE_PILOT_TANH, static_cast<const float2*>(Y_dev),
+        static_cast<const float2*>(G_dev),
         (long long)F * M, N, K * L, static_cast<float2*>(dY_dev), dp_dev, workspace_dev,
         workspace_bytes, static_cast<cudaStream_t>(stream)));
 }

@@ -46,16 +46,18 @@ QuantLayout quant_layout(long long A, int N, int dtype);
 // Launchers (return cudaSuccess or the launch error).
 cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s);
-cudaError_t launch_simt_real(const float* p, const float2* Y, long long A, int N, int KL,
-                             float2* H, cudaStream_t s);
+cudaError_t launch_simt_real(const float* p, bool tanh_map, const float2* Y, long long A, int N,
+                             int KL, float2* H, cudaStream_t s);
 cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* ws,
                             int32_t* exps, double* power, cudaStream_t s);
 // status: PNCE_OK, or PNCE_ECUDA / PNCE_EUNSUPPORTED
 pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
                       int KL, int dtype, const void* ws, float2* H, cudaStream_t s);
-cudaError_t launch_backward(const float* p, const float2* Y, const float2* G, long long A,
-                            int N, int KL, float2* dY, float* dp, void* ws, size_t ws_bytes,
-                            cudaStream_t s);
+cudaError_t launch_backward(const float* p, bool tanh_map, const float2* Y, const float2* G,
+                            long long A, int N, int KL, float2* dY, float* dp, void* ws,
+                            size_t ws_bytes, cudaStream_t s);
+cudaError_t launch_adjoint_dy(const float* p, bool tanh_map, const float2* G, long long A, int N,
+                              int KL, float2* dY, cudaStream_t s);
 size_t backward_workspace(long long A, int N, int KL);
 
 }  // namespace pnce

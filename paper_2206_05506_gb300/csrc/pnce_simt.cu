@@ -43,18 +43,21 @@ struct Smem {
     float2 y[2][TA][NC];
 };
 
-enum Mode { FWD_BITS = 0, FWD_REAL = 1, ADJ_REAL = 2 };
+// FWD_BITS: +-1 pilot from packed bits.  FWD_REAL / ADJ_REAL: float pilot, read forwards
+// or backwards.  *_TANH: the float argument is theta and the pilot is tanh(theta).
+enum Mode { FWD_BITS = 0, FWD_REAL = 1, ADJ_REAL = 2, FWD_TANH = 3, ADJ_TANH = 4 };
 
 template <int MODE>
 __device__ __forceinline__ float pilot_value(const uint32_t* bits, const float* preal, int q,
                                              int nmod) {
-    if constexpr (MODE == ADJ_REAL) {
-        return __ldg(preal + (q == 0 ? 0 : nmod - q));
-    } else if constexpr (MODE == FWD_BITS) {
+    if constexpr (MODE == FWD_BITS) {
         uint32_t b = (__ldg(bits + (q >> 5)) >> (q & 31)) & 1u;
         return b ? -1.0f : 1.0f;
     } else {
-        return __ldg(preal + q);
+        const int idx = (MODE == ADJ_REAL || MODE == ADJ_TANH) ? (q == 0 ? 0 : nmod - q) : q;
+        const float v = __ldg(preal + idx);
+        if constexpr (MODE == FWD_TANH || MODE == ADJ_TANH) return tanhf(v);
+        return v;
     }
 }
 
@@ -183,15 +186,17 @@ cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long
     return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Y, A, N, KL, N, H, s);
 }
 
-cudaError_t launch_simt_real(const float* p, const float2* Y, long long A, int N, int KL,
-                             float2* H, cudaStream_t s) {
-    return launch<FWD_REAL>(nullptr, p, Y, A, N, KL, N, H, s);
+cudaError_t launch_simt_real(const float* p, bool tanh_map, const float2* Y, long long A, int N,
+                             int KL, float2* H, cudaStream_t s) {
+    return tanh_map ? launch<FWD_TANH>(nullptr, p, Y, A, N, KL, N, H, s)
+                    : launch<FWD_REAL>(nullptr, p, Y, A, N, KL, N, H, s);
 }
 
-cudaError_t launch_adjoint_dy(const float* p, const float2* G, long long A, int N, int KL,
-                              float2* dY, cudaStream_t s) {
+cudaError_t launch_adjoint_dy(const float* p, bool tanh_map, const float2* G, long long A, int N,
+                              int KL, float2* dY, cudaStream_t s) {
     // reduction over the KL lags of G, N outputs per row, pilot read backwards
-    return launch<ADJ_REAL>(nullptr, p, G, A, KL, N, N, dY, s);
+    return tanh_map ? launch<ADJ_TANH>(nullptr, p, G, A, KL, N, N, dY, s)
+                    : launch<ADJ_REAL>(nullptr, p, G, A, KL, N, N, dY, s);
 }
 
 }  // namespace pnce

@@ -72,4 +72,5 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.pnce_destroy(None) == 1
     assert lib.pnce_pilot_destroy(None) == 1
     assert lib.pnce_estimate(None, None, None, 1, 1, 7, 1, 1, 0, None, 0, None, None) == 1
-    assert lib.pnce_backward(None, None, None, None, 1, 1, 7, 1, 1, None, None, None, 0, None) == 1
+    assert lib.pnce_backward(None, None, 0, None, None, 1, 1, 7, 1, 1, None, None, None, 0,
+                             None) == 1
