@@ -178,6 +178,30 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
                                void* workspace_dev, size_t workspace_bytes, void* H_host,
                                void* stream);
 
+/*
+ * Allocation-free estimate (no counterpart in the paper; an interface addition).  Same
+ * result as pnce_estimate for the tensor-core dtypes, but the call takes no workspace and
+ * allocates nothing: the quantised operand and factors live in one device array of
+ * PNCE_STATIC_SCRATCH_BYTES that is part of the library image.  It is for callers that
+ * cannot call cudaMalloc: a real-time receive chain whose per-slot deadline cannot absorb
+ * the allocator's unbounded latency (cudaMalloc may also synchronise the device), and
+ * hosts that run the library inside a fixed, pre-reserved memory budget with no allocator
+ * to hand it.
+ *  - Every device that loads the library keeps the array until the process exits.
+ *  - Shapes whose operand does not fit (pnce_workspace_size(...) > PNCE_STATIC_SCRATCH_BYTES,
+ *    e.g. more than about 2000 antennas at N = 4095 in fp16) return PNCE_EINVAL and launch
+ *    nothing; FP32_SIMT needs no scratch and is rejected here too (use pnce_estimate).
+ *  - The first call on a device looks up the array's device address; make that first call
+ *    before any stream capture.
+ *  - All calls share the one array and it keeps the last call's contents (nothing in it
+ *    needs to start at zero).  Calls whose work overlaps on the GPU -- other streams, other
+ *    threads, other handles -- race on it: the caller must serialise them.
+ */
+#define PNCE_STATIC_SCRATCH_BYTES (64u << 20)
+pnce_status pnce_estimate_static(pnce_handle* h, const pnce_pilot* pilot, const void* Y_dev,
+                                 int F, int M, int N, int K, int L, int dtype, void* H_dev,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

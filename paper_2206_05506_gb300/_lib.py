@@ -42,6 +42,7 @@ _SIGS = {
     "pnce_backward": (_i, [_vp, _vp, _i, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp, _vp, _sz, _vp]),
     "pnce_host_workspace_size": (_sz, [_i, _i, _i, _i, _i, _i]),
     "pnce_estimate_host": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
+    "pnce_estimate_static": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp]),
 }
 
 

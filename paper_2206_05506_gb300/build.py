@@ -20,7 +20,8 @@ BUILD_DIR = os.path.join(PKG_DIR, "_build")
 LIB_NAME = "libpnce.so"
 LIB_PATH = os.path.join(PKG_DIR, LIB_NAME)
 
-SOURCES = ["pnce_api.cu", "pnce_simt.cu", "pnce_quant.cu", "pnce_tc.cu", "pnce_adjoint.cu"]
+SOURCES = ["pnce_api.cu", "pnce_simt.cu", "pnce_quant.cu", "pnce_tc.cu", "pnce_adjoint.cu",
+           "pnce_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]
