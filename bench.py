@@ -69,44 +69,69 @@ def traffic_from_profile(workload: str, dtype: str, frames: int):
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons; keeps the samples that arrive
+    between mark_start() and mark_end() (plus one sampling period)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.lines = []
+        self.t0 = self.t1 = None
 
-    def start(self):
+    def start(self, warm_s: float = 1.0):
+        import threading
+
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.PERIOD_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.proc = None
+            return
+
+        def reader():
+            for line in self.proc.stdout:
+                self.lines.append((time.monotonic(), line))
+
+        threading.Thread(target=reader, daemon=True).start()
+        t_end = time.monotonic() + warm_s          # wait for the first samples to flow
+        while not self.lines and time.monotonic() < t_end:
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_end(self):
+        self.t1 = time.monotonic()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(self.PERIOD_MS / 1000.0 * 2)
         self.proc.terminate()
         try:
-            out, _ = self.proc.communicate(timeout=5)
+            self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-            out, _ = self.proc.communicate()
-        rows = [r.split(",") for r in out.strip().splitlines() if r.strip()]
-        sm, mx, reasons = [], None, set()
+        lo, hi = self.t0, self.t1 + self.PERIOD_MS / 1000.0
+        sm, mx, power, reasons = [], None, [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            r = [x.strip() for x in r]
+        for t, line in list(self.lines):
+            if not (lo <= t <= hi):
+                continue
+            r = [x.strip() for x in line.split(",")]
             if len(r) < 9:
                 continue
             try:
                 sm.append(float(r[1]))
                 mx = float(r[2])
+                power.append(float(r[3]))
             except ValueError:
                 continue
             for name, v in zip(names, r[5:9]):
@@ -115,6 +140,7 @@ class ClockSampler:
         if not sm:
             return None
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "samples": len(sm),
+                "power_w_median": float(np.median(power)) if power else None,
                 "reasons": sorted(reasons)}
 
 
@@ -175,7 +201,7 @@ def run_reference(args, w):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=C.PRECISION.name, choices=sorted(C.WORKLOADS))
@@ -224,44 +250,78 @@ def main():
         ws = torch.empty(pk.workspace_size(F, M, N, K, L, dt), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # Frame chunks: quantisation of chunk i+1 (stream sq) overlaps the correlation of chunk
+    # i (stream sc) -- the quantiser is HBM-bound, the correlation tensor-bound.  Same rule
+    # as pnce_estimate: chunks of >= 8 waves of 128 x 256 tiles, at most 4.
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    tiles = F * ((2 * M + 127) // 128) * ((K * L + 255) // 256)
+    nch = max(1, min(4, tiles // (8 * nsm), F)) if dt != "fp32" else 1
+    per = (F + nch - 1) // nch
+    chunks = [(f0, min(F, f0 + per)) for f0 in range(0, F, per)]
+    sq = torch.cuda.Stream(dev)
+    sc = torch.cuda.Stream(dev)
+    wss = [torch.empty(pk.workspace_size(f1 - f0, M, N, K, L, dt), dtype=torch.uint8, device=dev)
+           for f0, f1 in chunks] if dt != "fp32" else []
+    Ych = [Y[f0:f1] for f0, f1 in chunks]
+    Hch = [H[f0:f1] for f0, f1 in chunks]
+    q_done = [torch.cuda.Event() for _ in chunks]
+
     def step(ev=None):
-        if dt == "fp32":
-            if ev:
-                ev[0].record(stream)
-                ev[1].record(stream)
-            pk.estimate(Y, pilot, K, L, dtype="fp32", out=H)
-            if ev:
-                ev[2].record(stream)
-            return 1
+        """One pass of the estimator over the batch; ev = (start, [(c0, c1) per chunk], end)
+        events: start/end on the caller's stream, c0/c1 around each correlation launch on
+        the correlation stream."""
         if ev:
             ev[0].record(stream)
-        pk.quantize(Y, dt, workspace=ws)
-        if ev:
-            ev[1].record(stream)
-        pk.correlate_quantized(ws, pilot, F, M, K, L, dt, out=H)
+        if dt == "fp32":
+            if ev:
+                ev[1][0][0].record(stream)
+            pk.estimate(Y, pilot, K, L, dtype="fp32", out=H)
+            if ev:
+                ev[1][0][1].record(stream)
+                ev[2].record(stream)
+            return 1
+        sq.wait_stream(stream)
+        sc.wait_stream(stream)
+        for i, (f0, f1) in enumerate(chunks):
+            with torch.cuda.stream(sq):
+                pk.quantize(Ych[i], dt, workspace=wss[i])
+                q_done[i].record(sq)
+            with torch.cuda.stream(sc):
+                sc.wait_event(q_done[i])
+                if ev:
+                    ev[1][i][0].record(sc)
+                pk.correlate_quantized(wss[i], pilot, f1 - f0, M, K, L, dt, out=Hch[i])
+                if ev:
+                    ev[1][i][1].record(sc)
+        stream.wait_stream(sq)
+        stream.wait_stream(sc)
         if ev:
             ev[2].record(stream)
-        return 2
+        return 2 * len(chunks)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     assert pk.get_status(dev) == 0
 
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    def mk():
+        return torch.cuda.Event(enable_timing=True)
+
+    evs = [(mk(), [(mk(), mk()) for _ in chunks], mk()) for _ in range(args.steps)]
     clocks = ClockSampler(local)
+    clocks.start()
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    clocks.mark_start()
     launches = 0
     for i in range(args.steps):
         launches += step(evs[i])
     torch.cuda.synchronize()
+    clocks.mark_end()
     barrier()
     clk = clocks.stop()
-    step_ms = [evs[i][0].elapsed_time(evs[i][2]) for i in range(args.steps)]
-    corr_ms = [evs[i][1].elapsed_time(evs[i][2]) for i in range(args.steps)]
-    quant_ms = [evs[i][0].elapsed_time(evs[i][1]) for i in range(args.steps)]
+    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+    corr_ms = [c0.elapsed_time(c1) for e in evs for (c0, c1) in e[1]]
     total_ms = evs[0][0].elapsed_time(evs[-1][2])
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
@@ -304,7 +364,8 @@ def main():
 
     # ---- roofline of the correlation kernel
     peaks, peak_src = load_peaks()
-    flops = 4.0 * F * M * N * K * L          # real GEMM: 2FM rows x N x KL, 2 flop per MAC
+    # per correlation launch (one chunk): real GEMM of 2 Fc M rows x N x KL, 2 flop per MAC
+    flops = 4.0 * (F / len(chunks)) * M * N * K * L
     kern_ms = float(np.mean(corr_ms))
     if dt == "fp32":
         roof = None
@@ -314,7 +375,8 @@ def main():
         peak = base * DTYPE_RATIO[dt]
         achieved = flops / (kern_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic_from_profile(w.name, dt, F),
+                "frac": achieved / peak,
+                "traffic": traffic_from_profile(w.name, dt, F / len(chunks)),
                 "kernel": "tc_corr_kernel", "peak_source":
                 f"{peak_src} {'sustained' if long_region else 'burst'} bf16 x {DTYPE_RATIO[dt]}"}
 
@@ -337,8 +399,9 @@ def main():
         "config": {"workload": w.name, "frames": F, "M": M, "N": N, "K": K, "L": L,
                    "snr_db": list(w.snr_db), "parallelism": f"frames x{world}",
                    "l2": f"inputs larger than L2 ({Y.numel() * 8 / 1e9:.2f} GB Y per step)"},
-        "breakdown_ms": {"quantize": float(np.mean(quant_ms)), "correlate": kern_ms,
-                         "step_p50": float(np.median(step_ms))},
+        "breakdown_ms": {"correlate_per_launch": kern_ms,
+                         "correlate_sum_per_step": kern_ms * len(chunks),
+                         "step_p50": float(np.median(step_ms)), "chunks": len(chunks)},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "taps/s",
                 "h2d_bytes_per_step": int(Y_pin.numel() * 8),

@@ -37,6 +37,60 @@ pnce_status check_device(const pnce_handle* h) {
 
 pnce_status from_cuda(cudaError_t e) { return e == cudaSuccess ? PNCE_OK : PNCE_ECUDA; }
 
+// Frame chunks for pnce_estimate: a large batch is quantised chunk by chunk on one stream
+// while the tensor-core kernel correlates the previous chunk on another (the quantiser is
+// HBM-bound, the correlation tensor-bound, and their blocks fit on an SM together).  Each
+// chunk keeps >= 8 waves of 128 x 256 tiles so the per-launch tail stays small.
+int estimate_chunks(const pnce_handle* h, int F, int M, int N, int KL) {
+    (void)N;
+    const long long row_blocks_per_frame = (2LL * M + 127) / 128;
+    const long long jt = (KL + 255) / 256;
+    const long long tiles = (long long)F * row_blocks_per_frame * jt;
+    long long n = tiles / (8LL * h->num_sms);
+    if (n > 4) n = 4;
+    if (n > F) n = F;
+    return n < 2 ? 1 : (int)n;
+}
+
+pnce_status estimate_overlapped(pnce_handle* h, const pnce_pilot* pilot, const float2* Y, int F,
+                                int M, int N, int KL, int dtype, void* ws, float2* H,
+                                cudaStream_t user, int nch) {
+    const long long A = (long long)F * M;
+    const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
+    unsigned char* operand = static_cast<unsigned char*>(pnce::ws_operand(ws, lay));
+    float* factors = pnce::ws_factors(ws, lay);
+    const size_t row_bytes = (size_t)pnce::row_pitch(N) * pnce::elem_bytes(dtype);
+    // both pipeline streams start after the work already queued on the caller's stream
+    if (cudaEventRecord(h->ev_est_start, user) != cudaSuccess ||
+        cudaStreamWaitEvent(h->s_quant, h->ev_est_start, 0) != cudaSuccess ||
+        cudaStreamWaitEvent(h->s_corr, h->ev_est_start, 0) != cudaSuccess)
+        return PNCE_ECUDA;
+    const int per = (F + nch - 1) / nch;
+    int i = 0;
+    for (int f0 = 0; f0 < F; f0 += per, ++i) {
+        const int fc = (F - f0 < per) ? (F - f0) : per;
+        const long long a0 = (long long)f0 * M, ac = (long long)fc * M;
+        // chunk i owns operand rows [2 a0, 2 (a0 + ac)) and factors [a0, a0 + ac) of the
+        // whole-batch layout, so chunks never share memory
+        void* op = operand + (size_t)(2 * a0) * row_bytes;
+        float* fa = factors + a0;
+        if (pnce::launch_quantize(Y + a0 * N, ac, N, dtype, op, fa, nullptr, nullptr,
+                                  h->s_quant) != cudaSuccess ||
+            cudaEventRecord(h->ev_q[i], h->s_quant) != cudaSuccess ||
+            cudaStreamWaitEvent(h->s_corr, h->ev_q[i], 0) != cudaSuccess)
+            return PNCE_ECUDA;
+        pnce_status st = pnce::launch_tc(h, pilot, ac, N, KL, dtype, op, fa, H + a0 * KL, h->s_corr);
+        if (st != PNCE_OK) return st;
+    }
+    // the caller's stream resumes when both pipeline streams are done
+    if (cudaEventRecord(h->ev_est_done[0], h->s_quant) != cudaSuccess ||
+        cudaEventRecord(h->ev_est_done[1], h->s_corr) != cudaSuccess ||
+        cudaStreamWaitEvent(user, h->ev_est_done[0], 0) != cudaSuccess ||
+        cudaStreamWaitEvent(user, h->ev_est_done[1], 0) != cudaSuccess)
+        return PNCE_ECUDA;
+    return PNCE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -80,7 +134,14 @@ pnce_status pnce_create(pnce_handle** out) {
     ok = ok && cudaStreamCreateWithFlags(&h->s_h2d, sf) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&h->s_comp, sf) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&h->s_d2h, sf) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&h->s_quant, sf) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&h->s_corr, sf) == cudaSuccess;
     const unsigned ef = cudaEventDisableTiming;
+    for (int i = 0; i < 8 && ok; ++i)
+        ok = ok && cudaEventCreateWithFlags(&h->ev_q[i], ef) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&h->ev_est_start, ef) == cudaSuccess;
+    for (int i = 0; i < 2 && ok; ++i)
+        ok = ok && cudaEventCreateWithFlags(&h->ev_est_done[i], ef) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i) {
         ok = ok && cudaEventCreateWithFlags(&h->ev_in[i], ef) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&h->ev_comp[i], ef) == cudaSuccess;
@@ -99,8 +160,13 @@ pnce_status pnce_create(pnce_handle** out) {
 
 pnce_status pnce_destroy(pnce_handle* h) {
     if (!h) return PNCE_EINVAL;
-    for (cudaStream_t s : {h->s_h2d, h->s_comp, h->s_d2h})
+    for (cudaStream_t s : {h->s_h2d, h->s_comp, h->s_d2h, h->s_quant, h->s_corr})
         if (s) cudaStreamDestroy(s);
+    for (int i = 0; i < 8; ++i)
+        if (h->ev_q[i]) cudaEventDestroy(h->ev_q[i]);
+    if (h->ev_est_start) cudaEventDestroy(h->ev_est_start);
+    for (int i = 0; i < 2; ++i)
+        if (h->ev_est_done[i]) cudaEventDestroy(h->ev_est_done[i]);
     for (int i = 0; i < 2; ++i)
         for (cudaEvent_t e : {h->ev_in[i], h->ev_comp[i], h->ev_out[i]})
             if (e) cudaEventDestroy(e);
@@ -182,9 +248,11 @@ pnce_status pnce_quantize(pnce_handle* h, const void* Y_dev, int F, int M, int N
     if (workspace_bytes < pnce::quant_layout(A, N, dtype).total) return PNCE_EINVAL;
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
+    const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
     return from_cuda(pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
-                                           workspace_dev, exps_dev, power_dev,
-                                           static_cast<cudaStream_t>(stream)));
+                                           pnce::ws_operand(workspace_dev, lay),
+                                           pnce::ws_factors(workspace_dev, lay), exps_dev,
+                                           power_dev, static_cast<cudaStream_t>(stream)));
 }
 
 pnce_status pnce_correlate_quantized(pnce_handle* h, const pnce_pilot* pilot, int F, int M, int N,
@@ -198,8 +266,11 @@ pnce_status pnce_correlate_quantized(pnce_handle* h, const pnce_pilot* pilot, in
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
     if (pilot->device != h->device || pilot->N != N) return PNCE_ESTATE;
-    return pnce::launch_tc(h, pilot, A, N, K * L, dtype, workspace_dev,
-                           static_cast<float2*>(H_dev), static_cast<cudaStream_t>(stream));
+    const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
+    void* ws = const_cast<void*>(workspace_dev);
+    return pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(ws, lay),
+                           pnce::ws_factors(ws, lay), static_cast<float2*>(H_dev),
+                           static_cast<cudaStream_t>(stream));
 }
 
 pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y_dev, int F,
@@ -221,11 +292,20 @@ pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y
     if (!workspace_dev || !aligned16(workspace_dev)) return PNCE_EINVAL;
     if (workspace_bytes < pnce::quant_layout(A, N, dtype).total) return PNCE_EINVAL;
     if (!(h->cc_major == 10 && h->cc_minor == 3)) return PNCE_EUNSUPPORTED;
-    st = from_cuda(pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
-                                         workspace_dev, nullptr, nullptr, s));
-    if (st != PNCE_OK) return st;
-    return pnce::launch_tc(h, pilot, A, N, K * L, dtype, workspace_dev,
-                           static_cast<float2*>(H_dev), s);
+    const int nch = estimate_chunks(h, F, M, N, K * L);
+    if (nch <= 1) {
+        const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
+        st = from_cuda(pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
+                                             pnce::ws_operand(workspace_dev, lay),
+                                             pnce::ws_factors(workspace_dev, lay), nullptr,
+                                             nullptr, s));
+        if (st != PNCE_OK) return st;
+        return pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(workspace_dev, lay),
+                               pnce::ws_factors(workspace_dev, lay),
+                               static_cast<float2*>(H_dev), s);
+    }
+    return estimate_overlapped(h, pilot, static_cast<const float2*>(Y_dev), F, M, N, K * L, dtype,
+                               workspace_dev, static_cast<float2*>(H_dev), s, nch);
 }
 
 pnce_status pnce_estimate_real_pilot(pnce_handle* h, const float* p_dev, int pilot_map,
@@ -364,11 +444,15 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
             st = from_cuda(pnce::launch_simt_bits(pilot, static_cast<const float2*>(yd), A, N,
                                                   K * L, static_cast<float2*>(hd), h->s_comp));
         } else {
+            const pnce::QuantLayout ql = pnce::quant_layout(A, N, dtype);
+            void* q = ws + lay.q_off;
             st = from_cuda(pnce::launch_quantize(static_cast<const float2*>(yd), A, N, dtype,
-                                                 ws + lay.q_off, nullptr, nullptr, h->s_comp));
+                                                 pnce::ws_operand(q, ql), pnce::ws_factors(q, ql),
+                                                 nullptr, nullptr, h->s_comp));
             if (st == PNCE_OK)
-                st = pnce::launch_tc(h, pilot, A, N, K * L, dtype, ws + lay.q_off,
-                                     static_cast<float2*>(hd), h->s_comp);
+                st = pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(q, ql),
+                                     pnce::ws_factors(q, ql), static_cast<float2*>(hd),
+                                     h->s_comp);
         }
         if (st != PNCE_OK) return st;
         if (cudaEventRecord(h->ev_comp[b], h->s_comp) != cudaSuccess) return PNCE_ECUDA;

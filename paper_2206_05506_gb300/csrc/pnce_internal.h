@@ -17,6 +17,10 @@ struct pnce_handle {
     // and per double-buffer slot events
     cudaStream_t s_h2d, s_comp, s_d2h;
     cudaEvent_t ev_in[2], ev_comp[2], ev_out[2], ev_start, ev_done[3];
+    // pnce_estimate on large batches: quantisation of frame chunk i+1 (s_quant) overlaps
+    // the tensor-core correlation of chunk i (s_corr)
+    cudaStream_t s_quant, s_corr;
+    cudaEvent_t ev_q[8], ev_est_start, ev_est_done[2];
 };
 
 struct pnce_pilot {
@@ -48,11 +52,20 @@ cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long
                              int KL, float2* H, cudaStream_t s);
 cudaError_t launch_simt_real(const float* p, bool tanh_map, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s);
-cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* ws,
-                            int32_t* exps, double* power, cudaStream_t s);
+// operand: [2A][row_pitch(N)] elements; factors: float[A] (2^-s_a / N)
+cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* operand,
+                            float* factors, int32_t* exps, double* power, cudaStream_t s);
 // status: PNCE_OK, or PNCE_ECUDA / PNCE_EUNSUPPORTED
 pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
-                      int KL, int dtype, const void* ws, float2* H, cudaStream_t s);
+                      int KL, int dtype, const void* operand, const float* factors, float2* H,
+                      cudaStream_t s);
+// the two pointers of a workspace laid out by quant_layout
+inline void* ws_operand(void* ws, const QuantLayout& l) {
+    return static_cast<unsigned char*>(ws) + l.a_offset;
+}
+inline float* ws_factors(void* ws, const QuantLayout& l) {
+    return reinterpret_cast<float*>(static_cast<unsigned char*>(ws) + l.scale_offset);
+}
 cudaError_t launch_backward(const float* p, bool tanh_map, const float2* Y, const float2* G,
                             long long A, int N, int KL, float2* dY, float* dp, void* ws,
                             size_t ws_bytes, cudaStream_t s);

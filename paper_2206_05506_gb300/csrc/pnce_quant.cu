@@ -150,16 +150,13 @@ quantize_kernel(const float2* __restrict__ Y, long long A, int N, int pitch, voi
 }
 
 template <int DT>
-cudaError_t launch_dt(const float2* Y, long long A, int N, void* ws, int32_t* exps,
-                      double* power, cudaStream_t s) {
-    const pnce::QuantLayout lay = pnce::quant_layout(A, N, DT);
-    unsigned char* base = static_cast<unsigned char*>(ws);
+cudaError_t launch_dt(const float2* Y, long long A, int N, void* operand, float* factors,
+                      int32_t* exps, double* power, cudaStream_t s) {
     const float invN = (float)(1.0 / (double)N);
     if (A > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     auto kern = power ? quantize_kernel<DT, true> : quantize_kernel<DT, false>;
-    kern<<<(unsigned)A, THREADS, 0, s>>>(Y, A, N, pnce::row_pitch(N), base + lay.a_offset,
-                                         reinterpret_cast<float*>(base + lay.scale_offset),
-                                         exps, power, invN);
+    kern<<<(unsigned)A, THREADS, 0, s>>>(Y, A, N, pnce::row_pitch(N), operand, factors, exps,
+                                         power, invN);
     return cudaGetLastError();
 }
 
@@ -185,13 +182,14 @@ QuantLayout quant_layout(long long A, int N, int dtype) {
     return l;
 }
 
-cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* ws,
-                            int32_t* exps, double* power, cudaStream_t s) {
+cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* operand,
+                            float* factors, int32_t* exps, double* power, cudaStream_t s) {
     switch (dtype) {
-        case PNCE_FP16: return launch_dt<PNCE_FP16>(Y, A, N, ws, exps, power, s);
-        case PNCE_BF16: return launch_dt<PNCE_BF16>(Y, A, N, ws, exps, power, s);
-        case PNCE_TF32: return launch_dt<PNCE_TF32>(Y, A, N, ws, exps, power, s);
-        case PNCE_FP8E4M3: return launch_dt<PNCE_FP8E4M3>(Y, A, N, ws, exps, power, s);
+        case PNCE_FP16: return launch_dt<PNCE_FP16>(Y, A, N, operand, factors, exps, power, s);
+        case PNCE_BF16: return launch_dt<PNCE_BF16>(Y, A, N, operand, factors, exps, power, s);
+        case PNCE_TF32: return launch_dt<PNCE_TF32>(Y, A, N, operand, factors, exps, power, s);
+        case PNCE_FP8E4M3:
+            return launch_dt<PNCE_FP8E4M3>(Y, A, N, operand, factors, exps, power, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -61,8 +61,11 @@ extern "C" pnce_status pnce_estimate_static(pnce_handle* h, const pnce_pilot* pi
     // nothing in the scratch needs clearing: every row and factor the correlation reads is
     // rewritten by the quantiser first, and the pad columns past N are never read
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype, ws, nullptr,
+    const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
+    if (pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
+                              pnce::ws_operand(ws, lay), pnce::ws_factors(ws, lay), nullptr,
                               nullptr, s) != cudaSuccess)
         return PNCE_ECUDA;
-    return pnce::launch_tc(h, pilot, A, N, K * L, dtype, ws, static_cast<float2*>(H_dev), s);
+    return pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(ws, lay),
+                           pnce::ws_factors(ws, lay), static_cast<float2*>(H_dev), s);
 }

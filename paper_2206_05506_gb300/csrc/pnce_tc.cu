@@ -62,6 +62,8 @@ struct TcParams {
     int stages;             // pipeline depth (<= STAGES)
     int b_region;           // bytes of the pilot operand region
     int res_rows;           // resident pilot: 16-byte rows to generate (0 otherwise)
+    int drop_first_arrive;  // test hook: the per-stage pilot generator withholds its first
+                            // arrive, so the MMA issuer's bounded wait must run out
     unsigned long long wait_limit_ns;
     int* err;
 };
@@ -384,7 +386,8 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                 gen_pilot_rows<DT>(sB + stage * BSTAGE, ext, prm.N, s_start, rows, lane, 32);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&ctl->full_b[stage]);
+                const bool drop = prm.drop_first_arrive && t == blockIdx.x && kb == 0;
+                if (lane == 0 && !drop) mbar_arrive(&ctl->full_b[stage]);
                 if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
             }
         }
@@ -532,24 +535,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// Bound on every device-side wait (PNCE_WAIT_LIMIT_MS, default 2000 ms), read per launch.
 unsigned long long wait_limit_ns() {
-    static unsigned long long v = [] {
-        const char* e = getenv("PNCE_WAIT_LIMIT_MS");
-        long long ms = e ? atoll(e) : 2000;
-        if (ms < 1) ms = 1;
-        return (unsigned long long)ms * 1000000ull;
-    }();
-    return v;
+    const char* e = getenv("PNCE_WAIT_LIMIT_MS");
+    long long ms = e ? atoll(e) : 2000;
+    if (ms < 1) ms = 1;
+    return (unsigned long long)ms * 1000000ull;
 }
 
 template <int DT>
 pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N, int KL,
-                      const void* ws, float2* H, cudaStream_t s) {
+                      const void* operand, const float* factors, float2* H, cudaStream_t s) {
     using F = TcFmt<DT>;
     auto enc = encode_fn();
     if (!enc) return PNCE_ECUDA;
-    const pnce::QuantLayout lay = pnce::quant_layout(A, N, DT);
-    const unsigned char* wsb = static_cast<const unsigned char*>(ws);
 
     CUtensorMap map;
     CUtensorMapDataType ty = CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
@@ -560,7 +559,7 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     const cuuint64_t strides[1] = {(cuuint64_t)pnce::row_pitch(N) * pnce::elem_bytes(DT)};
     const cuuint32_t box[2] = {(cuuint32_t)F::BK, (cuuint32_t)BM};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&map, ty, 2, const_cast<unsigned char*>(wsb + lay.a_offset), dims, strides,
+    CUresult r = enc(&map, ty, 2, const_cast<void*>(operand), dims, strides,
                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return PNCE_ECUDA;
@@ -589,8 +588,12 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     const long long res_cm = (long long)(prm.BN / 8 - 1) * F::QS +
                              ((long long)prm.num_kb * (F::BK / F::EPR) - 1) * F::TS + 1;
     const long long res_bytes = (res_cm * 128 + 1023) / 1024 * 1024;
-    // PNCE_TC_STAGED_PILOT=1 forces the per-stage pilot path (used to test both paths)
+    // PNCE_TC_STAGED_PILOT=1 forces the per-stage pilot path (used to test both paths);
+    // PNCE_TC_TEST_DROP_ARRIVE=1 (staged path only) withholds one arrive so that the test of
+    // the bounded waits sees PNCE_ETIMEOUT latched and the context still usable
     const char* force = getenv("PNCE_TC_STAGED_PILOT");
+    const char* drop = getenv("PNCE_TC_TEST_DROP_ARRIVE");
+    prm.drop_first_arrive = (drop && drop[0] == '1') ? 1 : 0;
     const bool res = !(force && force[0] == '1') && (grid % prm.num_jt == 0) &&
                      (avail - res_bytes) / A_STAGE >= MIN_RES_STAGES;
     if (res) {
@@ -608,8 +611,7 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return PNCE_ECUDA;
-    kern<<<(unsigned)grid, THREADS, smem, s>>>(
-        map, pilot->ext_bits_dev, reinterpret_cast<const float*>(wsb + lay.scale_offset), H, prm);
+    kern<<<(unsigned)grid, THREADS, smem, s>>>(map, pilot->ext_bits_dev, factors, H, prm);
     return cudaGetLastError() == cudaSuccess ? PNCE_OK : PNCE_ECUDA;
 }
 
@@ -618,13 +620,15 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
 namespace pnce {
 
 pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N, int KL,
-                      int dtype, const void* ws, float2* H, cudaStream_t s) {
+                      int dtype, const void* operand, const float* factors, float2* H,
+                      cudaStream_t s) {
     if (!(h->cc_major == 10 && h->cc_minor == 3)) return PNCE_EUNSUPPORTED;
     switch (dtype) {
-        case PNCE_FP16: return launch_dt<PNCE_FP16>(h, pilot, A, N, KL, ws, H, s);
-        case PNCE_BF16: return launch_dt<PNCE_BF16>(h, pilot, A, N, KL, ws, H, s);
-        case PNCE_FP8E4M3: return launch_dt<PNCE_FP8E4M3>(h, pilot, A, N, KL, ws, H, s);
-        case PNCE_TF32: return launch_dt<PNCE_TF32>(h, pilot, A, N, KL, ws, H, s);
+        case PNCE_FP16: return launch_dt<PNCE_FP16>(h, pilot, A, N, KL, operand, factors, H, s);
+        case PNCE_BF16: return launch_dt<PNCE_BF16>(h, pilot, A, N, KL, operand, factors, H, s);
+        case PNCE_FP8E4M3:
+            return launch_dt<PNCE_FP8E4M3>(h, pilot, A, N, KL, operand, factors, H, s);
+        case PNCE_TF32: return launch_dt<PNCE_TF32>(h, pilot, A, N, KL, operand, factors, H, s);
         default: return PNCE_EINVAL;
     }
 }
