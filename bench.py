@@ -1,10 +1,13 @@
 """Benchmark: PN-correlation channel estimation throughput on GB300.
 
-One step = the whole estimator on one batch: per-antenna quantisation of the received
-blocks and the tensor-core correlation with its epilogue (pnce_quantize followed by
-pnce_correlate_quantized, the same two kernels pnce_estimate launches), on synthetic
-received blocks shaped like the precision workload (M=128 antennas, N=4095 m-sequence,
-K=16 transmitters x L=128 taps, 512 frames, SNR 0/10/20/30 dB), inputs resident in HBM.
+One step = one pnce_estimate call over one batch: per-antenna quantisation of the
+received blocks and the tensor-core correlation with its epilogue (for a batch this large
+the library overlaps the quantisation of frame chunk i+1 with the correlation of chunk i),
+on synthetic received blocks shaped like the precision workload (M=128 antennas, N=4095
+m-sequence, K=16 transmitters x L=128 taps, 512 frames, SNR 0/10/20/30 dB), inputs
+resident in HBM.  The library's tracing records CUDA events around each kernel it
+launches, on the stream the kernel runs on; the correlation kernels' durations give the
+roofline figure.
 
 value      CIR taps estimated per second (one tap = one complex H entry), all ranks
 e2e        the same metric through pnce_estimate_host: host (pinned) Y in, host H out
@@ -158,6 +161,50 @@ def cpu_oracle_sample(bits, Y_sample, K, L, target_s=15.0, max_frames=None):
     return nf, dt, H
 
 
+def run_serving(dev, seconds: float, rate_hz: float = 20000.0):
+    """Poisson request stream (uneven M, N, K, L) through the continuous-batching server,
+    tensor cores (fp16) and the plain FP32 SIMT path on the same trace."""
+    import torch
+
+    from oracle import pn_oracle as O
+    from paper_2206_05506_gb300 import serve
+    from synth import serving as S
+
+    pool = S.payload_pool(slots=4, seed=0)
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in pool.items()}
+    specs = S.poisson_trace(rate_hz, seconds, seed=0, payload_slots=4)
+    ring_elems = 64 << 20                      # 512 MB of page-locked results, reused in turn
+    ring = torch.zeros(ring_elems, dtype=torch.complex64, pin_memory=True)
+    res = {"rate_hz": rate_hz, "seconds": seconds, "requests": len(specs)}
+    for dtype, name in (("fp16", "fp16_tensor_core"), ("fp32", "fp32_simt")):
+        eng = serve.GpuEngine(S.pilot_bits, device=dev, dtype=dtype, slots=4)
+        eng.prepare([255, 511, 1023, 2047])
+        reqs, off = [], 0
+        for sp in specs:
+            n = sp.M * sp.K * sp.L
+            if off + n > ring_elems:
+                off = 0
+            y = pinned[(sp.M, sp.N)]
+            r = serve.Request(sp.rid, sp.t_arrival, sp.M, sp.N, sp.K, sp.L,
+                              y.data_ptr() + sp.slot * sp.M * sp.N * 8, ring.data_ptr() + off * 8)
+            r.off = off
+            reqs.append(r)
+            off += n
+        serve.Server(eng).run([serve.Request(-1, 0.0, r.M, r.N, r.K, r.L, r.y_addr, r.h_addr)
+                               for r in reqs[:200]])            # warm the path
+        srv = serve.Server(eng, mem_cap_bytes=40e9)
+        st = srv.run(reqs)
+        # accuracy of the last requests (their results are still in the ring)
+        errs = []
+        for r in reqs[-16:]:
+            H = ring[r.off:r.off + r.M * r.K * r.L].numpy().reshape(1, r.M, r.K, r.L)
+            Y = pool[(r.M, r.N)][[specs[r.rid].slot]]
+            errs.append(O.nmse(H, O.estimate(Y, S.pilot_bits(r.N), r.K, r.L)))
+        st["nmse_max_last16"] = float(max(errs))
+        res[name] = st
+    return res
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -210,6 +257,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ref-frames", type=int, default=2, help="frames per reference step")
+    ap.add_argument("--serving-seconds", type=float, default=1.0,
+                    help="length of the Poisson serving trace (0: skip)")
     args = ap.parse_args()
 
     w = C.WORKLOADS[args.workload]
@@ -250,84 +299,46 @@ def main():
         ws = torch.empty(pk.workspace_size(F, M, N, K, L, dt), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    # Frame chunks: quantisation of chunk i+1 (stream sq) overlaps the correlation of chunk
-    # i (stream sc) -- the quantiser is HBM-bound, the correlation tensor-bound.  Same rule
-    # as pnce_estimate: chunks of >= 8 waves of 128 x 256 tiles, at most 4.
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    tiles = F * ((2 * M + 127) // 128) * ((K * L + 255) // 256)
-    nch = max(1, min(4, tiles // (8 * nsm), F)) if dt != "fp32" else 1
-    per = (F + nch - 1) // nch
-    chunks = [(f0, min(F, f0 + per)) for f0 in range(0, F, per)]
-    sq = torch.cuda.Stream(dev)
-    sc = torch.cuda.Stream(dev)
-    wss = [torch.empty(pk.workspace_size(f1 - f0, M, N, K, L, dt), dtype=torch.uint8, device=dev)
-           for f0, f1 in chunks] if dt != "fp32" else []
-    Ych = [Y[f0:f1] for f0, f1 in chunks]
-    Hch = [H[f0:f1] for f0, f1 in chunks]
-    q_done = [torch.cuda.Event() for _ in chunks]
+    def step():
+        # the product call: pnce_estimate; for large batches it overlaps the quantisation of
+        # frame chunk i+1 with the tensor-core correlation of chunk i on internal streams
+        pk.estimate(Y, pilot, K, L, dtype=dt, out=H, workspace=ws)
 
-    def step(ev=None):
-        """One pass of the estimator over the batch; ev = (start, [(c0, c1) per chunk], end)
-        events: start/end on the caller's stream, c0/c1 around each correlation launch on
-        the correlation stream."""
-        if ev:
-            ev[0].record(stream)
-        if dt == "fp32":
-            if ev:
-                ev[1][0][0].record(stream)
-            pk.estimate(Y, pilot, K, L, dtype="fp32", out=H)
-            if ev:
-                ev[1][0][1].record(stream)
-                ev[2].record(stream)
-            return 1
-        sq.wait_stream(stream)
-        sc.wait_stream(stream)
-        for i, (f0, f1) in enumerate(chunks):
-            with torch.cuda.stream(sq):
-                pk.quantize(Ych[i], dt, workspace=wss[i])
-                q_done[i].record(sq)
-            with torch.cuda.stream(sc):
-                sc.wait_event(q_done[i])
-                if ev:
-                    ev[1][i][0].record(sc)
-                pk.correlate_quantized(wss[i], pilot, f1 - f0, M, K, L, dt, out=Hch[i])
-                if ev:
-                    ev[1][i][1].record(sc)
-        stream.wait_stream(sq)
-        stream.wait_stream(sc)
-        if ev:
-            ev[2].record(stream)
-        return 2 * len(chunks)
-
+    pk.trace_enable(True, dev)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     assert pk.get_status(dev) == 0
+    pk.trace_read(dev)
 
-    def mk():
-        return torch.cuda.Event(enable_timing=True)
-
-    evs = [(mk(), [(mk(), mk()) for _ in chunks], mk()) for _ in range(args.steps)]
+    e_start = torch.cuda.Event(enable_timing=True)
+    e_end = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     clocks.start()
     barrier()
     torch.cuda.synchronize()
     clocks.mark_start()
-    launches = 0
+    e_start.record(stream)
     for i in range(args.steps):
-        launches += step(evs[i])
+        step()
+    e_end.record(stream)
     torch.cuda.synchronize()
     clocks.mark_end()
     barrier()
     clk = clocks.stop()
-    step_ms = [e[0].elapsed_time(e[2]) for e in evs]
-    corr_ms = [c0.elapsed_time(c1) for e in evs for (c0, c1) in e[1]]
-    total_ms = evs[0][0].elapsed_time(evs[-1][2])
+    trace = pk.trace_read(dev)       # (kind, ms) of every kernel launched in the timed region
+    pk.trace_enable(False, dev)
+    total_ms = e_start.elapsed_time(e_end)
     t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
     assert pk.get_status(dev) == 0
+    main_kind = "simt" if dt == "fp32" else "correlate"
+    corr_ms = [ms for kind, ms in trace if kind == main_kind]
+    quant_ms = [ms for kind, ms in trace if kind == "quantize"]
+    launches = len(trace)
+    nch = max(1, len(corr_ms) // args.steps)
 
     taps_per_step = F * M * K * L
     value = taps_per_step * args.steps * world / (total_ms / 1e3)
@@ -364,11 +375,19 @@ def main():
 
     # ---- roofline of the correlation kernel
     peaks, peak_src = load_peaks()
-    # per correlation launch (one chunk): real GEMM of 2 Fc M rows x N x KL, 2 flop per MAC
-    flops = 4.0 * (F / len(chunks)) * M * N * K * L
+    # per correlation launch (one frame chunk): real GEMM of 2 Fc M rows x N x KL, 2 flop
+    # per MAC (the SIMT path does the same 2 FMA per complex sample and lag)
+    flops = 4.0 * (F / nch) * M * N * K * L
     kern_ms = float(np.mean(corr_ms))
     if dt == "fp32":
-        roof = None
+        # FP32 CUDA-core peak: 152 SMs x 128 FMA lanes x 2 flop x SM clock (2070 MHz max)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = (clk or {}).get("sm_mhz") or 2070.0
+        peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+        achieved = flops / (kern_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "simt_corr_kernel",
+                "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"}
     else:
         long_region = total_ms > 1000.0
         base = peaks["bf16_tflops_sustained" if long_region else "bf16_tflops"]
@@ -376,7 +395,7 @@ def main():
         achieved = flops / (kern_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "traffic": traffic_from_profile(w.name, dt, F / len(chunks)),
+                "traffic": traffic_from_profile(w.name, dt, F / nch),
                 "kernel": "tc_corr_kernel", "peak_source":
                 f"{peak_src} {'sustained' if long_region else 'burst'} bf16 x {DTYPE_RATIO[dt]}"}
 
@@ -391,6 +410,8 @@ def main():
                "sample": f"first {nf} of {F} frames, FP64 Toeplitz product (numpy BLAS)"}
         nmse = O.nmse(H[:nf].cpu().numpy(), Href)
 
+    serving = run_serving(dev, args.serving_seconds) if args.serving_seconds > 0 else None
+
     line = {
         "metric": "CIR taps estimated/s", "value": value, "unit": "taps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -400,8 +421,9 @@ def main():
                    "snr_db": list(w.snr_db), "parallelism": f"frames x{world}",
                    "l2": f"inputs larger than L2 ({Y.numel() * 8 / 1e9:.2f} GB Y per step)"},
         "breakdown_ms": {"correlate_per_launch": kern_ms,
-                         "correlate_sum_per_step": kern_ms * len(chunks),
-                         "step_p50": float(np.median(step_ms)), "chunks": len(chunks)},
+                         "correlate_launches_per_step": nch,
+                         "quantize_per_launch": float(np.mean(quant_ms)) if quant_ms else 0.0,
+                         "traced_kernels": launches},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "taps/s",
                 "h2d_bytes_per_step": int(Y_pin.numel() * 8),
@@ -411,6 +433,7 @@ def main():
         "clocks": clk,
         "nmse_vs_oracle": nmse,
         "cpu_baseline": cpu,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -179,6 +179,37 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
                                void* stream);
 
 /*
+ * Tracing.  While enabled, the estimate entry points (pnce_estimate, pnce_quantize,
+ * pnce_correlate_quantized) record a CUDA event before and after every kernel they launch,
+ * on the stream that kernel runs on (internal streams included), up to 8192 kernels.
+ * pnce_trace_enable creates the events on first use (allocates host and event resources,
+ * not device memory) and clears the record; pnce_trace_read waits for the recorded kernels,
+ * returns up to max_entries (kind, milliseconds) pairs -- kind 0 quantiser, 1 tensor-core
+ * correlation, 2 FP32 SIMT correlation -- in launch order, and clears the record.  Do not
+ * enable it while capturing a CUDA graph.
+ */
+pnce_status pnce_trace_enable(pnce_handle* h, int on);
+pnce_status pnce_trace_read(pnce_handle* h, int* kinds, float* ms, int max_entries, int* count);
+
+/*
+ * Row movement for batched serving (the frames of many requests estimated as one batch;
+ * no counterpart in the paper, which processes one frame at a time).  Pointer tables are
+ * arrays of 64-bit addresses that the GPU can dereference: device memory, or page-locked
+ * host memory, which the kernels then read or write directly over the host link.  The
+ * tables themselves may also live in page-locked host memory.  A NULL row address skips
+ * that row.  Both calls only enqueue one kernel on `stream`.
+ *
+ * pnce_gather_rows: dst_dev[r][0..nelem) = src_rows[r][0..nelem) for r < rows, with
+ *   8-byte elements (one complex64 sample) and a row pitch of dst_pitch elements.
+ * pnce_scatter_rows: dst_rows[r][0..counts[r]) = src_dev[r][0..counts[r]) for r < rows,
+ *   source row pitch src_pitch elements (counts are clamped to src_pitch).
+ */
+pnce_status pnce_gather_rows(const uint64_t* src_rows, int rows, int nelem, void* dst_dev,
+                             long long dst_pitch, void* stream);
+pnce_status pnce_scatter_rows(const void* src_dev, long long src_pitch, const uint64_t* dst_rows,
+                              const int* counts, int rows, void* stream);
+
+/*
  * Allocation-free estimate (no counterpart in the paper; an interface addition).  Same
  * result as pnce_estimate for the tensor-core dtypes, but the call takes no workspace and
  * allocates nothing: the quantised operand and factors live in one device array of

@@ -28,6 +28,7 @@ from ._lib import DTYPES, PnceError, check
 __all__ = ["Pilot", "Context", "estimate", "quantize", "correlate_quantized",
            "estimate_real_pilot", "backward", "estimate_host", "PILOT_MAPS", "workspace_size",
            "host_workspace_size", "backward_workspace_size", "get_status", "DTYPES",
+           "trace_enable", "trace_read",
            "PnceError", "lib"]
 
 
@@ -90,6 +91,26 @@ def context(device=None) -> Context:
         if idx not in _contexts:
             _contexts[idx] = Context(idx)
         return _contexts[idx]
+
+
+def trace_enable(on: bool = True, device=None):
+    """Record CUDA events around every kernel the estimate entry points launch."""
+    ctx = context(device)
+    check(lib().pnce_trace_enable(ctx.handle, 1 if on else 0), "pnce_trace_enable")
+
+
+TRACE_KINDS = {0: "quantize", 1: "correlate", 2: "simt"}
+
+
+def trace_read(device=None, max_entries: int = 8192):
+    """[(kind, ms)] of the kernels traced since the last read (waits for them)."""
+    ctx = context(device)
+    kinds = (C.c_int * max_entries)()
+    ms = (C.c_float * max_entries)()
+    n = C.c_int(0)
+    check(lib().pnce_trace_read(ctx.handle, kinds, ms, max_entries, C.byref(n)),
+          "pnce_trace_read")
+    return [(TRACE_KINDS.get(kinds[i], str(kinds[i])), float(ms[i])) for i in range(n.value)]
 
 
 def get_status(device=None) -> int:

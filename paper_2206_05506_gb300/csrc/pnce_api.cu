@@ -41,6 +41,15 @@ pnce_status from_cuda(cudaError_t e) { return e == cudaSuccess ? PNCE_OK : PNCE_
 // while the tensor-core kernel correlates the previous chunk on another (the quantiser is
 // HBM-bound, the correlation tensor-bound, and their blocks fit on an SM together).  Each
 // chunk keeps >= 8 waves of 128 x 256 tiles so the per-launch tail stays small.
+// Quantiser grid while it overlaps a correlation: PNCE_QUANT_BLOCKS_PER_SM blocks per SM,
+// default 0 = one block per antenna (measured on GB300, 512 x 128 x 4095 fp16: 1.65 ms per
+// estimate uncapped, 1.96 / 1.73 / 1.67 ms with 1 / 2 / 4 blocks per SM).
+int quant_blocks_overlapped(const pnce_handle* h) {
+    const char* e = getenv("PNCE_QUANT_BLOCKS_PER_SM");
+    const int per = e ? atoi(e) : 0;
+    return per > 0 ? per * h->num_sms : 0;
+}
+
 int estimate_chunks(const pnce_handle* h, int F, int M, int N, int KL) {
     (void)N;
     const long long row_blocks_per_frame = (2LL * M + 127) / 128;
@@ -74,11 +83,16 @@ pnce_status estimate_overlapped(pnce_handle* h, const pnce_pilot* pilot, const f
         // whole-batch layout, so chunks never share memory
         void* op = operand + (size_t)(2 * a0) * row_bytes;
         float* fa = factors + a0;
-        if (pnce::launch_quantize(Y + a0 * N, ac, N, dtype, op, fa, nullptr, nullptr,
-                                  h->s_quant) != cudaSuccess ||
-            cudaEventRecord(h->ev_q[i], h->s_quant) != cudaSuccess ||
+        cudaError_t e;
+        {
+            pnce::TraceScope tr(h, h->s_quant, pnce::TRACE_QUANTIZE);
+            e = pnce::launch_quantize(Y + a0 * N, ac, N, dtype, op, fa, nullptr, nullptr,
+                                      h->s_quant, i == 0 ? 0 : quant_blocks_overlapped(h));
+        }
+        if (e != cudaSuccess || cudaEventRecord(h->ev_q[i], h->s_quant) != cudaSuccess ||
             cudaStreamWaitEvent(h->s_corr, h->ev_q[i], 0) != cudaSuccess)
             return PNCE_ECUDA;
+        pnce::TraceScope tr(h, h->s_corr, pnce::TRACE_CORRELATE);
         pnce_status st = pnce::launch_tc(h, pilot, ac, N, KL, dtype, op, fa, H + a0 * KL, h->s_corr);
         if (st != PNCE_OK) return st;
     }
@@ -173,8 +187,49 @@ pnce_status pnce_destroy(pnce_handle* h) {
     if (h->ev_start) cudaEventDestroy(h->ev_start);
     for (int i = 0; i < 3; ++i)
         if (h->ev_done[i]) cudaEventDestroy(h->ev_done[i]);
+    if (h->trace_ev) {
+        for (int i = 0; i < 2 * pnce::kTraceMax; ++i)
+            if (h->trace_ev[i]) cudaEventDestroy(h->trace_ev[i]);
+        delete[] h->trace_ev;
+        delete[] h->trace_kind;
+    }
     if (h->status_dev) cudaFree(h->status_dev);
     delete h;
+    return PNCE_OK;
+}
+
+pnce_status pnce_trace_enable(pnce_handle* h, int on) {
+    if (!h) return PNCE_EINVAL;
+    if (on && !h->trace_ev) {
+        pnce_status st = check_device(h);
+        if (st != PNCE_OK) return st;
+        h->trace_ev = new (std::nothrow) cudaEvent_t[2 * pnce::kTraceMax]();
+        h->trace_kind = new (std::nothrow) int[pnce::kTraceMax]();
+        if (!h->trace_ev || !h->trace_kind) return PNCE_ENOMEM;
+        for (int i = 0; i < 2 * pnce::kTraceMax; ++i)
+            if (cudaEventCreate(&h->trace_ev[i]) != cudaSuccess) return PNCE_ECUDA;
+    }
+    h->trace_on = on ? 1 : 0;
+    h->trace_n = 0;
+    return PNCE_OK;
+}
+
+pnce_status pnce_trace_read(pnce_handle* h, int* kinds, float* ms, int max_entries, int* count) {
+    if (!h || !count || max_entries < 0 || (max_entries > 0 && (!kinds || !ms)))
+        return PNCE_EINVAL;
+    *count = 0;
+    if (!h->trace_ev) return PNCE_OK;
+    const int n = h->trace_n < max_entries ? h->trace_n : max_entries;
+    for (int i = 0; i < n; ++i) {
+        if (cudaEventSynchronize(h->trace_ev[2 * i + 1]) != cudaSuccess) return PNCE_ECUDA;
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, h->trace_ev[2 * i], h->trace_ev[2 * i + 1]) != cudaSuccess)
+            return PNCE_ECUDA;
+        kinds[i] = h->trace_kind[i];
+        ms[i] = t;
+    }
+    *count = n;
+    h->trace_n = 0;
     return PNCE_OK;
 }
 
@@ -249,6 +304,7 @@ pnce_status pnce_quantize(pnce_handle* h, const void* Y_dev, int F, int M, int N
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
     const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
+    pnce::TraceScope tr(h, static_cast<cudaStream_t>(stream), pnce::TRACE_QUANTIZE);
     return from_cuda(pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
                                            pnce::ws_operand(workspace_dev, lay),
                                            pnce::ws_factors(workspace_dev, lay), exps_dev,
@@ -268,6 +324,7 @@ pnce_status pnce_correlate_quantized(pnce_handle* h, const pnce_pilot* pilot, in
     if (pilot->device != h->device || pilot->N != N) return PNCE_ESTATE;
     const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
     void* ws = const_cast<void*>(workspace_dev);
+    pnce::TraceScope tr(h, static_cast<cudaStream_t>(stream), pnce::TRACE_CORRELATE);
     return pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(ws, lay),
                            pnce::ws_factors(ws, lay), static_cast<float2*>(H_dev),
                            static_cast<cudaStream_t>(stream));
@@ -286,6 +343,7 @@ pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y
     const long long A = (long long)F * M;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (dtype == PNCE_FP32_SIMT) {
+        pnce::TraceScope tr(h, s, pnce::TRACE_SIMT);
         return from_cuda(pnce::launch_simt_bits(pilot, static_cast<const float2*>(Y_dev), A, N,
                                                 K * L, static_cast<float2*>(H_dev), s));
     }
@@ -295,11 +353,15 @@ pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y
     const int nch = estimate_chunks(h, F, M, N, K * L);
     if (nch <= 1) {
         const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
-        st = from_cuda(pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
-                                             pnce::ws_operand(workspace_dev, lay),
-                                             pnce::ws_factors(workspace_dev, lay), nullptr,
-                                             nullptr, s));
+        {
+            pnce::TraceScope tr(h, s, pnce::TRACE_QUANTIZE);
+            st = from_cuda(pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
+                                                 pnce::ws_operand(workspace_dev, lay),
+                                                 pnce::ws_factors(workspace_dev, lay), nullptr,
+                                                 nullptr, s));
+        }
         if (st != PNCE_OK) return st;
+        pnce::TraceScope tr(h, s, pnce::TRACE_CORRELATE);
         return pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(workspace_dev, lay),
                                pnce::ws_factors(workspace_dev, lay),
                                static_cast<float2*>(H_dev), s);

@@ -21,7 +21,34 @@ struct pnce_handle {
     // the tensor-core correlation of chunk i (s_corr)
     cudaStream_t s_quant, s_corr;
     cudaEvent_t ev_q[8], ev_est_start, ev_est_done[2];
+    // tracing (pnce_trace_enable): start/end events around each kernel the estimate entry
+    // points launch, recorded on the stream the kernel runs on
+    int trace_on;
+    int trace_n;
+    cudaEvent_t* trace_ev;              // 2 * kTraceMax events, created on first enable
+    int* trace_kind;
 };
+
+namespace pnce {
+constexpr int kTraceMax = 8192;
+enum TraceKind { TRACE_QUANTIZE = 0, TRACE_CORRELATE = 1, TRACE_SIMT = 2 };
+// Records a start event before / an end event after one kernel launch when tracing is on.
+struct TraceScope {
+    pnce_handle* h;
+    cudaStream_t s;
+    int slot;
+    TraceScope(pnce_handle* h_, cudaStream_t s_, int kind) : h(h_), s(s_), slot(-1) {
+        if (h && h->trace_on && h->trace_n < kTraceMax) {
+            slot = h->trace_n++;
+            h->trace_kind[slot] = kind;
+            cudaEventRecord(h->trace_ev[2 * slot], s);
+        }
+    }
+    ~TraceScope() {
+        if (slot >= 0) cudaEventRecord(h->trace_ev[2 * slot + 1], s);
+    }
+};
+}  // namespace pnce
 
 struct pnce_pilot {
     int device;
@@ -52,9 +79,11 @@ cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long
                              int KL, float2* H, cudaStream_t s);
 cudaError_t launch_simt_real(const float* p, bool tanh_map, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s);
-// operand: [2A][row_pitch(N)] elements; factors: float[A] (2^-s_a / N)
+// operand: [2A][row_pitch(N)] elements; factors: float[A] (2^-s_a / N).  max_blocks > 0
+// caps the grid (blocks then loop over antennas), to leave room for a concurrent kernel.
 cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* operand,
-                            float* factors, int32_t* exps, double* power, cudaStream_t s);
+                            float* factors, int32_t* exps, double* power, cudaStream_t s,
+                            int max_blocks = 0);
 // status: PNCE_OK, or PNCE_ECUDA / PNCE_EUNSUPPORTED
 pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
                       int KL, int dtype, const void* operand, const float* factors, float2* H,

@@ -88,10 +88,10 @@ quantize_kernel(const float2* __restrict__ Y, long long A, int N, int pitch, voi
     __shared__ float s_max[THREADS / 32];
     __shared__ double s_pow[THREADS / 32];
     __shared__ float s_scale;
-
-    const long long a = blockIdx.x;
-    const float2* row = Y + a * N;
     const int tid = threadIdx.x;
+
+  for (long long a = blockIdx.x; a < A; a += gridDim.x) {
+    const float2* row = Y + a * N;
 
     float amax = 0.f;
     double e = 0.0;
@@ -147,16 +147,20 @@ quantize_kernel(const float2* __restrict__ Y, long long A, int N, int pitch, voi
         store4<DT>(Q, 2 * a, pitch, n, re, valid);
         store4<DT>(Q, 2 * a + 1, pitch, n, im, valid);
     }
+    __syncthreads();   // s_max / s_scale are reused by the next antenna
+  }
 }
 
 template <int DT>
 cudaError_t launch_dt(const float2* Y, long long A, int N, void* operand, float* factors,
-                      int32_t* exps, double* power, cudaStream_t s) {
+                      int32_t* exps, double* power, cudaStream_t s, int max_blocks) {
     const float invN = (float)(1.0 / (double)N);
-    if (A > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    long long grid = A;
+    if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
+    if (grid > 0x7fffffffLL) grid = 0x7fffffffLL;
     auto kern = power ? quantize_kernel<DT, true> : quantize_kernel<DT, false>;
-    kern<<<(unsigned)A, THREADS, 0, s>>>(Y, A, N, pnce::row_pitch(N), operand, factors, exps,
-                                         power, invN);
+    kern<<<(unsigned)grid, THREADS, 0, s>>>(Y, A, N, pnce::row_pitch(N), operand, factors, exps,
+                                            power, invN);
     return cudaGetLastError();
 }
 
@@ -183,13 +187,14 @@ QuantLayout quant_layout(long long A, int N, int dtype) {
 }
 
 cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* operand,
-                            float* factors, int32_t* exps, double* power, cudaStream_t s) {
+                            float* factors, int32_t* exps, double* power, cudaStream_t s,
+                            int mb) {
     switch (dtype) {
-        case PNCE_FP16: return launch_dt<PNCE_FP16>(Y, A, N, operand, factors, exps, power, s);
-        case PNCE_BF16: return launch_dt<PNCE_BF16>(Y, A, N, operand, factors, exps, power, s);
-        case PNCE_TF32: return launch_dt<PNCE_TF32>(Y, A, N, operand, factors, exps, power, s);
+        case PNCE_FP16: return launch_dt<PNCE_FP16>(Y, A, N, operand, factors, exps, power, s, mb);
+        case PNCE_BF16: return launch_dt<PNCE_BF16>(Y, A, N, operand, factors, exps, power, s, mb);
+        case PNCE_TF32: return launch_dt<PNCE_TF32>(Y, A, N, operand, factors, exps, power, s, mb);
         case PNCE_FP8E4M3:
-            return launch_dt<PNCE_FP8E4M3>(Y, A, N, operand, factors, exps, power, s);
+            return launch_dt<PNCE_FP8E4M3>(Y, A, N, operand, factors, exps, power, s, mb);
         default: return cudaErrorInvalidValue;
     }
 }

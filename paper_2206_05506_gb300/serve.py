@@ -1,0 +1,295 @@
+"""Continuous-batching estimation server.
+
+Requests are single frames of uneven shape (M antennas, PN length N, K transmitters, L
+taps) whose received blocks sit in page-locked host memory.  The loop
+
+* admits arrivals while the bytes of admitted, unfinished work stay under a memory cap;
+* buckets admitted requests by (N, lag class) -- requests of one bucket share a pilot and
+  a padded lag count, so their antennas can be estimated as one batch;
+* whenever a stream slot is free, launches the bucket whose oldest request has waited
+  longest, packing as many of its requests as fit one batch: requests that arrive while
+  other batches are on the GPU join the next batch, and up to `slots` batches run
+  concurrently on their own streams;
+* runs each batch as one replay of a CUDA graph captured once per (slot, N, lag class,
+  capacity): gather the requests' antenna rows from host memory into the batch buffer,
+  estimate (quantise + tensor-core correlation, or the FP32 SIMT path), scatter each
+  antenna's lags straight into its request's host result buffer;
+* polls the batches' events and stamps each request's completion; latency is completion
+  minus scheduled arrival.
+
+Pilot tables and the per-shape buffers stay resident on the device.  Each request's result
+depends only on its own antenna rows (per-antenna scales, fixed reduction order), so it is
+the same alone and in any mix.
+"""
+from __future__ import annotations
+
+import collections
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import DTYPES, Pilot, check, context, lib, workspace_size
+
+KL_CLASSES = (64, 256, 1024)
+CAPACITIES = (64, 256, 1024, 4096)        # antennas per batch
+
+
+def kl_class(KL: int, N: int) -> int:
+    for c in KL_CLASSES:
+        if c >= KL:
+            return min(c, N)
+    return min(((KL + 1023) // 1024) * 1024, N)
+
+
+@dataclass
+class Request:
+    rid: int
+    t_arrival: float
+    M: int
+    N: int
+    K: int
+    L: int
+    y_addr: int               # address of complex64 [M][N] (host page-locked or device)
+    h_addr: int               # address of complex64 [M][K*L] for the result
+    nbytes: int = 0
+    t_admit: float = -1.0
+    t_launch: float = -1.0
+    t_done: float = -1.0
+    batch: int = -1
+
+
+@dataclass
+class _Busy:
+    slot: int
+    token: object
+    reqs: list
+    bid: int
+
+
+class Server:
+    """Scheduling and admission, independent of how a batch is executed (`engine`)."""
+
+    def __init__(self, engine, mem_cap_bytes: float = 40e9, max_batch_rows: int = 4096):
+        self.engine = engine
+        self.cap = float(mem_cap_bytes)
+        self.max_rows = max_batch_rows
+        self.pending: collections.deque = collections.deque()
+        self.buckets: dict[tuple, collections.deque] = {}
+        self.inflight_bytes = 0
+        self.peak_inflight_bytes = 0
+        self.free_slots = list(range(engine.slots))[::-1]
+        self.busy: list[_Busy] = []
+        self.done: list[Request] = []
+        self.batches = 0
+        self.batch_rows: list[int] = []
+
+    # -- arrivals and admission
+    def submit(self, req: Request):
+        req.nbytes = self.engine.footprint(req)
+        self.pending.append(req)
+
+    def _admit(self, now: float):
+        while self.pending:
+            r = self.pending[0]
+            if self.inflight_bytes + r.nbytes > self.cap and self.inflight_bytes > 0:
+                break                                   # wait for memory to free up
+            self.pending.popleft()
+            self.inflight_bytes += r.nbytes
+            self.peak_inflight_bytes = max(self.peak_inflight_bytes, self.inflight_bytes)
+            r.t_admit = now
+            key = (r.N, kl_class(r.K * r.L, r.N))
+            self.buckets.setdefault(key, collections.deque()).append(r)
+
+    # -- completions
+    def _complete(self, now: float):
+        still = []
+        for b in self.busy:
+            if self.engine.done(b.token):
+                for r in b.reqs:
+                    r.t_done = now
+                    self.inflight_bytes -= r.nbytes
+                    self.done.append(r)
+                self.free_slots.append(b.slot)
+            else:
+                still.append(b)
+        self.busy = still
+
+    # -- launches
+    def _launch(self, now: float):
+        while self.free_slots:
+            heads = [(q[0].t_arrival, key) for key, q in self.buckets.items() if q]
+            if not heads:
+                return
+            _, key = min(heads)
+            q = self.buckets[key]
+            reqs, rows = [], 0
+            while q and rows + q[0].M <= self.max_rows:
+                r = q.popleft()
+                reqs.append(r)
+                rows += r.M
+            if not reqs:                               # a single request above max_rows
+                reqs.append(q.popleft())
+                rows = reqs[0].M
+            slot = self.free_slots.pop()
+            for r in reqs:
+                r.t_launch = now
+                r.batch = self.batches
+            token = self.engine.launch(slot, key[0], key[1], reqs)
+            self.busy.append(_Busy(slot, token, reqs, self.batches))
+            self.batches += 1
+            self.batch_rows.append(rows)
+
+    def poll(self, now: float):
+        self._complete(now)
+        self._admit(now)
+        self._launch(now)
+
+    def idle(self) -> bool:
+        return not (self.pending or self.busy or any(self.buckets.values()))
+
+    def run(self, requests: list, clock=time.perf_counter, t0: float | None = None):
+        """Open loop: each request is submitted at its t_arrival (seconds from t0)."""
+        t0 = clock() if t0 is None else t0
+        i, n = 0, len(requests)
+        while i < n or not self.idle():
+            now = clock() - t0
+            while i < n and requests[i].t_arrival <= now:
+                self.submit(requests[i])
+                i += 1
+            self.poll(now)
+        return self.stats()
+
+    def stats(self) -> dict:
+        lat = np.array([r.t_done - r.t_arrival for r in self.done])
+        if lat.size == 0:
+            return {"requests": 0}
+        t_first = min(r.t_arrival for r in self.done)
+        t_last = max(r.t_done for r in self.done)
+        taps = sum(r.M * r.K * r.L for r in self.done)
+        span = max(t_last - t_first, 1e-9)
+        return {"requests": int(lat.size), "batches": self.batches,
+                "mean_batch_rows": float(np.mean(self.batch_rows)) if self.batch_rows else 0.0,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3),
+                "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "max_ms": float(lat.max() * 1e3),
+                "frames_per_s": lat.size / span, "taps_per_s": taps / span,
+                "peak_inflight_bytes": int(self.peak_inflight_bytes)}
+
+
+class _Shape:
+    """Device buffers, descriptor tables and the captured graph of one batch shape."""
+
+    def __init__(self, eng: "GpuEngine", slot: int, N: int, klc: int, cap: int):
+        dev = eng.device
+        self.N, self.klc, self.cap = N, klc, cap
+        self.Y = torch.zeros((1, cap, N), dtype=torch.complex64, device=dev)
+        self.H = torch.zeros((1, cap, 1, klc), dtype=torch.complex64, device=dev)
+        need = workspace_size(1, cap, N, 1, klc, eng.dt)
+        self.ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
+        # descriptor tables in page-locked host memory: the kernels read them directly
+        self.src = torch.zeros(cap, dtype=torch.int64, pin_memory=True)
+        self.dst = torch.zeros(cap, dtype=torch.int64, pin_memory=True)
+        self.cnt = torch.zeros(cap, dtype=torch.int32, pin_memory=True)
+        self.src_np, self.dst_np, self.cnt_np = self.src.numpy(), self.dst.numpy(), self.cnt.numpy()
+        self.pilot = eng.pilot(N)
+        self.graph = None
+        stream = eng.streams[slot]
+        if eng.use_graphs:
+            with torch.cuda.stream(stream):
+                self._enqueue(eng, stream.cuda_stream)      # eager run: sets kernel attributes
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=stream):
+                self._enqueue(eng, torch.cuda.current_stream(dev).cuda_stream)
+            self.graph = g
+
+    def _enqueue(self, eng: "GpuEngine", s: int):
+        L = lib()
+        check(L.pnce_gather_rows(self.src.data_ptr(), self.cap, self.N, self.Y.data_ptr(),
+                                 self.N, s), "pnce_gather_rows")
+        check(L.pnce_estimate(eng.ctx.handle, self.pilot.handle, self.Y.data_ptr(), 1, self.cap,
+                              self.N, 1, self.klc, eng.dt, self.ws.data_ptr(), self.ws.numel(),
+                              self.H.data_ptr(), s), "pnce_estimate")
+        check(L.pnce_scatter_rows(self.H.data_ptr(), self.klc, self.dst.data_ptr(),
+                                  self.cnt.data_ptr(), self.cap, s), "pnce_scatter_rows")
+
+    def run(self, eng: "GpuEngine", slot: int, reqs: list):
+        rows = 0
+        for r in reqs:
+            m = np.arange(r.M, dtype=np.int64)
+            self.src_np[rows:rows + r.M] = r.y_addr + m * (r.N * 8)
+            self.dst_np[rows:rows + r.M] = r.h_addr + m * (r.K * r.L * 8)
+            self.cnt_np[rows:rows + r.M] = r.K * r.L
+            rows += r.M
+        self.src_np[rows:] = 0
+        self.dst_np[rows:] = 0
+        self.cnt_np[rows:] = 0
+        stream = eng.streams[slot]
+        with torch.cuda.stream(stream):
+            if self.graph is not None:
+                self.graph.replay()
+            else:
+                self._enqueue(eng, stream.cuda_stream)
+
+
+class GpuEngine:
+    """Executes batches with libpnce on one device: `slots` streams, graphs per shape."""
+
+    def __init__(self, pilot_bits, device=None, dtype="fp16", slots: int = 3,
+                 use_graphs: bool = True):
+        """pilot_bits: callable N -> 0/1 array, the m-sequence used for PN length N."""
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index)
+        self.dt = DTYPES[dtype]
+        self.dtype = dtype
+        self.slots = slots
+        self.use_graphs = use_graphs
+        self.ctx = context(self.device)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(slots)]
+        self.events = [torch.cuda.Event() for _ in range(slots)]
+        self._pilots: dict[int, Pilot] = {}
+        self._shapes: dict[tuple, _Shape] = {}
+        self._pilot_bits = pilot_bits
+        self.elt = {0: 0, 1: 4, 2: 2, 3: 2, 4: 1}[self.dt]
+
+    def pilot(self, N: int) -> Pilot:
+        if N not in self._pilots:
+            self._pilots[N] = Pilot(self._pilot_bits(N), device=self.device)
+        return self._pilots[N]
+
+    def footprint(self, r: Request) -> int:
+        pitch = (r.N + 63) // 64 * 64
+        return r.M * (8 * r.N + 2 * self.elt * pitch + 8 * kl_class(r.K * r.L, r.N))
+
+    def prepare(self, Ns, caps=CAPACITIES[:3]):
+        """Create (and capture) the batch shapes of every (N, lag class) bucket of the given
+        PN lengths, for every slot, before serving starts."""
+        for N in Ns:
+            for klc in sorted({kl_class(k, N) for k in KL_CLASSES if k <= N} | {kl_class(N, N)}):
+                for slot in range(self.slots):
+                    for c in caps:
+                        self._shape(slot, N, klc, c)
+
+    def _shape(self, slot, N, klc, cap) -> _Shape:
+        key = (slot, N, klc, cap)
+        if key not in self._shapes:
+            with torch.cuda.device(self.device):
+                self._shapes[key] = _Shape(self, slot, N, klc, cap)
+        return self._shapes[key]
+
+    def launch(self, slot: int, N: int, klc: int, reqs: list):
+        rows = sum(r.M for r in reqs)
+        cap = next((c for c in CAPACITIES if c >= rows), None)
+        if cap is None:
+            cap = (rows + 4095) // 4096 * 4096
+        shape = self._shape(slot, N, klc, cap)
+        shape.run(self, slot, reqs)
+        ev = self.events[slot]
+        ev.record(self.streams[slot])
+        return ev
+
+    @staticmethod
+    def done(token) -> bool:
+        return token.query()
