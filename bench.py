@@ -254,7 +254,7 @@ def main():
     ap.add_argument("--workload", default=C.PRECISION.name, choices=sorted(C.WORKLOADS))
     ap.add_argument("--dtype", default="fp16", choices=["fp32", "tf32", "fp16", "bf16", "e4m3"])
     ap.add_argument("--frames", type=int, default=None, help="override frames per step")
-    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ref-frames", type=int, default=2, help="frames per reference step")
     ap.add_argument("--serving-seconds", type=float, default=1.0,
@@ -343,6 +343,21 @@ def main():
     taps_per_step = F * M * K * L
     value = taps_per_step * args.steps * world / (total_ms / 1e3)
 
+    # the correlation kernel alone (operand quantised once, nothing running beside it), for
+    # comparison with its in-step duration above
+    alone_ms = None
+    if dt != "fp32":
+        q = pk.quantize(Y, dt, workspace=ws)
+        for _ in range(3):
+            pk.correlate_quantized(ws, pilot, F, M, K, L, dt, out=H)
+        pk.trace_enable(True, dev)
+        pk.trace_read(dev)
+        for _ in range(20):
+            pk.correlate_quantized(ws, pilot, F, M, K, L, dt, out=H)
+        alone_ms = float(np.mean([ms for _, ms in pk.trace_read(dev)]))
+        pk.trace_enable(False, dev)
+        del q
+
     # ---- end to end through the host-buffer entry point
     H_pin = torch.empty((F, M, K, L), dtype=torch.complex64, pin_memory=True)
     hws = torch.empty(pk.host_workspace_size(F, M, N, K, L, dt), dtype=torch.uint8, device=dev)
@@ -393,8 +408,11 @@ def main():
         base = peaks["bf16_tflops_sustained" if long_region else "bf16_tflops"]
         peak = base * DTYPE_RATIO[dt]
         achieved = flops / (kern_ms / 1e3) / 1e12
+        alone = 4.0 * F * M * N * K * L / (alone_ms / 1e3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
+                "kernel_alone": {"ms_per_launch": alone_ms, "frames_per_launch": F,
+                                 "achieved": alone, "frac": alone / peak},
                 "traffic": traffic_from_profile(w.name, dt, F / nch),
                 "kernel": "tc_corr_kernel", "peak_source":
                 f"{peak_src} {'sustained' if long_region else 'burst'} bf16 x {DTYPE_RATIO[dt]}"}

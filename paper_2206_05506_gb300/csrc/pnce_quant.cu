@@ -139,7 +139,7 @@ quantize_kernel(const float2* __restrict__ Y, long long A, int N, int pitch, voi
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             if (i < valid) {
-                const float2 y = row[n + i];
+                const float2 y = __ldcs(row + n + i);   // last use: evict first
                 re[i] = y.x * sc;          // exact: power-of-two scale
                 im[i] = y.y * sc;
             }
