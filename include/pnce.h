@@ -103,6 +103,33 @@ pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y
                           void* workspace_dev, size_t workspace_bytes, void* H_dev,
                           void* stream);
 
+/* Cyclic-shift rule of the multiplexed transmitters (Sec. II-B). */
+typedef enum {
+    PNCE_SHIFT_KL = 0,      /* transmitter k at cyclic shift k*L: lags 0 .. K*L-1 contiguous */
+    PNCE_SHIFT_SPREAD = 1   /* transmitter k at cyclic shift k*floor(N/K) (Eq. 8, spread evenly) */
+} pnce_shift_rule;
+
+/* Frame layout options of pnce_estimate_ex. */
+typedef struct {
+    int cp_len;             /* cyclic-prefix samples at the head of every received row */
+    int shift_rule;         /* a pnce_shift_rule */
+} pnce_frame_opts;
+
+/*
+ * pnce_estimate with the pilot-slot layout spelled out (Sec. II-A/B):
+ *  - Y_dev rows hold cp_len + N samples, the cyclic prefix first; the prefix is skipped
+ *    (Sec. II-A: the CP is removed and only the PN part is correlated);
+ *  - transmitter k uses the cyclic shift s_k given by opts->shift_rule, and
+ *    H[f][m][k][l] = (1/N) sum_n Y[f][m][cp_len + n] p[(n - s_k - l) mod N].
+ * Requires L <= floor(N/K) for PNCE_SHIFT_SPREAD (shifted copies must not alias, Eq. 7),
+ * K*L <= N for PNCE_SHIFT_KL.  opts == NULL is pnce_estimate.  Workspace as
+ * pnce_workspace_size(F, M, N, K, L, dtype).
+ */
+pnce_status pnce_estimate_ex(pnce_handle* h, const pnce_pilot* pilot, const void* Y_dev,
+                             int F, int M, int N, int K, int L, int dtype,
+                             const pnce_frame_opts* opts, void* workspace_dev,
+                             size_t workspace_bytes, void* H_dev, void* stream);
+
 /*
  * Reduced-precision operand (Sec. III-B: conversion of the received block to the
  * tensor-core input format).  For antenna a = f*M + m: A_a = max_n max(|Re y|, |Im y|)

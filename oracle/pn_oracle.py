@@ -105,6 +105,33 @@ def estimate(Y, bits, K: int, L: int) -> np.ndarray:
     return estimate_real_pilot(Y, pilot_symbols(bits), K, L)
 
 
+def estimate_general(Y, bits, K: int, L: int, cp_len: int = 0, shifts=None) -> np.ndarray:
+    """Estimator for rows that still carry a cyclic prefix and/or other cyclic shifts.
+
+    Y[f, m, cp_len + n] holds received sample n after the prefix (Sec. II-A: the CP is
+    removed before correlating); transmitter k uses the cyclic shift shifts[k] (default
+    k*L; Eq. 8 spreads them evenly).  H_hat[f,m,k,l] = (1/N) sum_n y[n] p[(n - shifts[k] - l)
+    mod N]: the correlator of Eq. 3 evaluated at the lags shifts[k] + l.
+    """
+    Y = np.asarray(Y)
+    if Y.ndim != 3:
+        raise ValueError("Y must be [F, M, cp_len + N]")
+    p = pilot_symbols(bits)
+    N = p.size
+    if Y.shape[-1] != cp_len + N:
+        raise ValueError("rows must hold cp_len + N samples")
+    sh = np.arange(K) * L if shifts is None else np.asarray(shifts, dtype=np.int64)
+    lags = (sh[:, None] + np.arange(L)[None, :]).reshape(-1)
+    if np.unique(lags % N).size != lags.size:
+        raise ValueError("the lag sets of different transmitters overlap (aliasing)")
+    y = Y[..., cp_len:].astype(np.complex128)
+    F, M, _ = y.shape
+    P = p[(np.arange(N)[:, None] - lags[None, :]) % N]
+    rows = y.reshape(F * M, N)
+    H = (rows.real @ P + 1j * (rows.imag @ P)) / N
+    return H.reshape(F, M, K, L)
+
+
 def estimate_fft(Y, bits, K: int, L: int) -> np.ndarray:
     """O3: circular cross-correlation by DFT, ifft(fft(y) * conj(fft(p))) / N, lags < K*L."""
     Y = np.asarray(Y).astype(np.complex128)

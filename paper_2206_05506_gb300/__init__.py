@@ -191,10 +191,24 @@ def _check_y(Y: torch.Tensor, pilot: Pilot | None = None):
     return Y.shape
 
 
+SHIFT_RULES = {"kl": 0, "spread": 1}
+
+
 def estimate(Y: torch.Tensor, pilot: Pilot, K: int, L: int, dtype="fp32", out=None,
-             workspace: torch.Tensor | None = None) -> torch.Tensor:
-    """Channel estimate H [F, M, K, L] (complex64) of received blocks Y [F, M, N]."""
-    F, M, N = _check_y(Y, pilot)
+             workspace: torch.Tensor | None = None, cp_len: int = 0,
+             shift_rule: str = "kl") -> torch.Tensor:
+    """Channel estimate H [F, M, K, L] (complex64) of received blocks Y [F, M, cp_len + N].
+
+    cp_len: cyclic-prefix samples at the head of each row (skipped).  shift_rule: "kl"
+    (transmitter k at cyclic shift k*L) or "spread" (k*floor(N/K), Eq. 8).
+    """
+    if cp_len == 0 and shift_rule == "kl":
+        F, M, N = _check_y(Y, pilot)
+    else:
+        F, M, T = _check_y(Y)
+        N = pilot.N
+        if T != cp_len + N:
+            raise ValueError(f"rows hold {T} samples, expected cp_len + N = {cp_len + N}")
     dt = _dt(dtype)
     dev = Y.device
     H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
@@ -202,9 +216,15 @@ def estimate(Y: torch.Tensor, pilot: Pilot, K: int, L: int, dtype="fp32", out=No
     ws = workspace if workspace is not None else _workspace(dev, need)
     nbytes = 0 if ws is None else ws.numel() * ws.element_size()
     with torch.cuda.device(dev):
-        check(lib().pnce_estimate(pilot.ctx.handle, pilot.handle, Y.data_ptr(), F, M, N, K, L,
-                                  dt, _ptr(ws), nbytes, H.data_ptr(), _stream(dev)),
-              "pnce_estimate")
+        if cp_len == 0 and shift_rule == "kl":
+            check(lib().pnce_estimate(pilot.ctx.handle, pilot.handle, Y.data_ptr(), F, M, N, K,
+                                      L, dt, _ptr(ws), nbytes, H.data_ptr(), _stream(dev)),
+                  "pnce_estimate")
+        else:
+            opts = _lib.FrameOpts(cp_len, SHIFT_RULES[shift_rule])
+            check(lib().pnce_estimate_ex(pilot.ctx.handle, pilot.handle, Y.data_ptr(), F, M, N,
+                                         K, L, dt, C.byref(opts), _ptr(ws), nbytes, H.data_ptr(),
+                                         _stream(dev)), "pnce_estimate_ex")
     return H
 
 

@@ -25,6 +25,12 @@ class PnceError(RuntimeError):
 _lib = None
 
 _vp, _i, _sz = C.c_void_p, C.c_int, C.c_size_t
+
+
+class FrameOpts(C.Structure):
+    """pnce_frame_opts"""
+    _fields_ = [("cp_len", C.c_int), ("shift_rule", C.c_int)]
+
 _SIGS = {
     "pnce_version": (_i, []),
     "pnce_status_string": (C.c_char_p, [_i]),
@@ -35,6 +41,8 @@ _SIGS = {
     "pnce_pilot_destroy": (_i, [_vp]),
     "pnce_workspace_size": (_sz, [_i, _i, _i, _i, _i, _i]),
     "pnce_estimate": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
+    "pnce_estimate_ex": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, C.POINTER(FrameOpts), _vp,
+                              _sz, _vp, _vp]),
     "pnce_quantize": (_i, [_vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp, _vp, _vp]),
     "pnce_correlate_quantized": (_i, [_vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
     "pnce_estimate_real_pilot": (_i, [_vp, _vp, _i, _vp, _i, _i, _i, _i, _i, _vp, _vp]),

@@ -370,6 +370,52 @@ pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y
                                workspace_dev, static_cast<float2*>(H_dev), s, nch);
 }
 
+pnce_status pnce_estimate_ex(pnce_handle* h, const pnce_pilot* pilot, const void* Y_dev, int F,
+                             int M, int N, int K, int L, int dtype, const pnce_frame_opts* opts,
+                             void* workspace_dev, size_t workspace_bytes, void* H_dev,
+                             void* stream) {
+    if (!opts)
+        return pnce_estimate(h, pilot, Y_dev, F, M, N, K, L, dtype, workspace_dev,
+                             workspace_bytes, H_dev, stream);
+    if (!h || !pilot || !Y_dev || !H_dev) return PNCE_EINVAL;
+    if (opts->cp_len < 0 || (opts->shift_rule != PNCE_SHIFT_KL &&
+                             opts->shift_rule != PNCE_SHIFT_SPREAD))
+        return PNCE_EINVAL;
+    if (!shape_ok(F, M, N, K, L)) return PNCE_EINVAL;
+    if (opts->shift_rule == PNCE_SHIFT_SPREAD && L > N / K) return PNCE_EINVAL;
+    if (!aligned16(Y_dev) || !aligned16(H_dev)) return PNCE_EINVAL;
+    if (dtype != PNCE_FP32_SIMT && !is_tc(dtype)) return PNCE_EINVAL;
+    pnce_status st = check_device(h);
+    if (st != PNCE_OK) return st;
+    if (pilot->device != h->device || pilot->N != N) return PNCE_ESTATE;
+    const long long A = (long long)F * M;
+    const long long stride = (long long)N + opts->cp_len;
+    const float2* Y = static_cast<const float2*>(Y_dev) + opts->cp_len;
+    const pnce::LagMap lm = opts->shift_rule == PNCE_SHIFT_KL
+                                ? pnce::lagmap_contiguous(K * L)
+                                : pnce::LagMap{1, K, L, N / K, K * L};
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    float2* H = static_cast<float2*>(H_dev);
+    if (dtype == PNCE_FP32_SIMT) {
+        pnce::TraceScope tr(h, s, pnce::TRACE_SIMT);
+        return from_cuda(pnce::launch_simt_bits_ex(pilot, Y, stride, A, N, lm, H, s));
+    }
+    if (!workspace_dev || !aligned16(workspace_dev)) return PNCE_EINVAL;
+    const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
+    if (workspace_bytes < lay.total) return PNCE_EINVAL;
+    if (!(h->cc_major == 10 && h->cc_minor == 3)) return PNCE_EUNSUPPORTED;
+    {
+        pnce::TraceScope tr(h, s, pnce::TRACE_QUANTIZE);
+        st = from_cuda(pnce::launch_quantize(Y, A, N, dtype, pnce::ws_operand(workspace_dev, lay),
+                                             pnce::ws_factors(workspace_dev, lay), nullptr,
+                                             nullptr, s, 0, stride));
+    }
+    if (st != PNCE_OK) return st;
+    pnce::TraceScope tr(h, s, pnce::TRACE_CORRELATE);
+    return pnce::launch_tc_ex(h, pilot, A, N, lm, dtype, pnce::ws_operand(workspace_dev, lay),
+                              pnce::ws_factors(workspace_dev, lay), H, s);
+}
+
 pnce_status pnce_estimate_real_pilot(pnce_handle* h, const float* p_dev, int pilot_map,
                                      const void* Y_dev, int F, int M, int N, int K, int L,
                                      void* H_dev, void* stream) {

@@ -59,6 +59,39 @@ struct pnce_pilot {
 
 namespace pnce {
 
+// Which correlation lags a launch computes and where they go in H.  Mode 0: the lags
+// j = 0 .. ldH-1, stored at column j (transmitter k at cyclic shift k*L).  Mode 1:
+// transmitter k at cyclic shift k*step; its lags k*step + l, l < L, stored at column
+// k*L + l.  Kernels cut the lags into tiles of `tile` consecutive lags.
+struct LagMap {
+    int mode;
+    int K, L;
+    int step;
+    int ldH;        // H row pitch in complex elements (= K*L)
+};
+inline LagMap lagmap_contiguous(int KL) { return LagMap{0, 1, KL, 0, KL}; }
+__host__ __device__ inline long long lag_tiles(const LagMap& m, int tile) {
+    return m.mode == 0 ? (m.ldH + tile - 1) / tile
+                       : (long long)m.K * ((m.L + tile - 1) / tile);
+}
+// tile jt: first lag (origin), first output column and number of valid lags
+__host__ __device__ inline void lag_tile(const LagMap& m, int tile, long long jt, long long& origin,
+                                         int& col0, int& valid) {
+    if (m.mode == 0) {
+        origin = jt * tile;
+        col0 = (int)origin;
+        const int rest = m.ldH - col0;
+        valid = rest < tile ? rest : tile;
+    } else {
+        const int tpk = (m.L + tile - 1) / tile;
+        const int k = (int)(jt / tpk), lb = (int)(jt % tpk);
+        origin = (long long)k * m.step + (long long)lb * tile;
+        col0 = k * m.L + lb * tile;
+        const int rest = m.L - lb * tile;
+        valid = rest < tile ? rest : tile;
+    }
+}
+
 // Elements of a quantised row are padded to a multiple of this (TMA row pitch).
 constexpr int kRowPad = 64;
 
@@ -77,17 +110,24 @@ QuantLayout quant_layout(long long A, int N, int dtype);
 // Launchers (return cudaSuccess or the launch error).
 cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s);
+// general form: rows of Y y_stride elements apart (first sample at Y), lags per `lags`
+cudaError_t launch_simt_bits_ex(const pnce_pilot* pilot, const float2* Y, long long y_stride,
+                                long long A, int N, const LagMap& lags, float2* H,
+                                cudaStream_t s);
 cudaError_t launch_simt_real(const float* p, bool tanh_map, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s);
 // operand: [2A][row_pitch(N)] elements; factors: float[A] (2^-s_a / N).  max_blocks > 0
 // caps the grid (blocks then loop over antennas), to leave room for a concurrent kernel.
 cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* operand,
                             float* factors, int32_t* exps, double* power, cudaStream_t s,
-                            int max_blocks = 0);
+                            int max_blocks = 0, long long y_stride = 0 /* 0: N */);
 // status: PNCE_OK, or PNCE_ECUDA / PNCE_EUNSUPPORTED
 pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
                       int KL, int dtype, const void* operand, const float* factors, float2* H,
                       cudaStream_t s);
+pnce_status launch_tc_ex(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
+                         const LagMap& lags, int dtype, const void* operand,
+                         const float* factors, float2* H, cudaStream_t s);
 // the two pointers of a workspace laid out by quant_layout
 inline void* ws_operand(void* ws, const QuantLayout& l) {
     return static_cast<unsigned char*>(ws) + l.a_offset;

@@ -82,7 +82,8 @@ __device__ __forceinline__ void store4(void* base, long long row, int pitch, int
 
 template <int DT, bool POW>
 __global__ void __launch_bounds__(THREADS)
-quantize_kernel(const float2* __restrict__ Y, long long A, int N, int pitch, void* __restrict__ Q,
+quantize_kernel(const float2* __restrict__ Y, long long A, int N, long long y_stride, int pitch,
+                void* __restrict__ Q,
                 float* __restrict__ out_scale, int32_t* __restrict__ exps,
                 double* __restrict__ power, float invN) {
     __shared__ float s_max[THREADS / 32];
@@ -91,7 +92,7 @@ quantize_kernel(const float2* __restrict__ Y, long long A, int N, int pitch, voi
     const int tid = threadIdx.x;
 
   for (long long a = blockIdx.x; a < A; a += gridDim.x) {
-    const float2* row = Y + a * N;
+    const float2* row = Y + a * y_stride;
 
     float amax = 0.f;
     double e = 0.0;
@@ -153,14 +154,16 @@ quantize_kernel(const float2* __restrict__ Y, long long A, int N, int pitch, voi
 
 template <int DT>
 cudaError_t launch_dt(const float2* Y, long long A, int N, void* operand, float* factors,
-                      int32_t* exps, double* power, cudaStream_t s, int max_blocks) {
+                      int32_t* exps, double* power, cudaStream_t s, int max_blocks,
+                      long long y_stride) {
     const float invN = (float)(1.0 / (double)N);
     long long grid = A;
     if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
     if (grid > 0x7fffffffLL) grid = 0x7fffffffLL;
     auto kern = power ? quantize_kernel<DT, true> : quantize_kernel<DT, false>;
-    kern<<<(unsigned)grid, THREADS, 0, s>>>(Y, A, N, pnce::row_pitch(N), operand, factors, exps,
-                                            power, invN);
+    kern<<<(unsigned)grid, THREADS, 0, s>>>(Y, A, N, y_stride > 0 ? y_stride : N,
+                                            pnce::row_pitch(N), operand, factors, exps, power,
+                                            invN);
     return cudaGetLastError();
 }
 
@@ -188,13 +191,16 @@ QuantLayout quant_layout(long long A, int N, int dtype) {
 
 cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* operand,
                             float* factors, int32_t* exps, double* power, cudaStream_t s,
-                            int mb) {
+                            int mb, long long ys) {
     switch (dtype) {
-        case PNCE_FP16: return launch_dt<PNCE_FP16>(Y, A, N, operand, factors, exps, power, s, mb);
-        case PNCE_BF16: return launch_dt<PNCE_BF16>(Y, A, N, operand, factors, exps, power, s, mb);
-        case PNCE_TF32: return launch_dt<PNCE_TF32>(Y, A, N, operand, factors, exps, power, s, mb);
+        case PNCE_FP16:
+            return launch_dt<PNCE_FP16>(Y, A, N, operand, factors, exps, power, s, mb, ys);
+        case PNCE_BF16:
+            return launch_dt<PNCE_BF16>(Y, A, N, operand, factors, exps, power, s, mb, ys);
+        case PNCE_TF32:
+            return launch_dt<PNCE_TF32>(Y, A, N, operand, factors, exps, power, s, mb, ys);
         case PNCE_FP8E4M3:
-            return launch_dt<PNCE_FP8E4M3>(Y, A, N, operand, factors, exps, power, s, mb);
+            return launch_dt<PNCE_FP8E4M3>(Y, A, N, operand, factors, exps, power, s, mb, ys);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -64,19 +64,21 @@ __device__ __forceinline__ float pilot_value(const uint32_t* bits, const float* 
 template <int MODE>
 __global__ void __launch_bounds__(256, 2)
 simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ preal,
-                 const float2* __restrict__ Y, long long A, int N /* reduction length */,
-                 int KL /* outputs per row */, int nmod, int num_jt, float invN,
-                 float2* __restrict__ H) {
+                 const float2* __restrict__ Y, long long y_stride, long long A,
+                 int N /* reduction length */, const pnce::LagMap lags, int nmod, int num_jt,
+                 float invN, float2* __restrict__ H) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long bid = blockIdx.x;
-    const int j0 = (int)(bid % num_jt) * TJ;
+    long long j0;            // first lag of this block's tile
+    int col0, valid;         // its first output column and number of lags kept
+    pnce::lag_tile(lags, TJ, bid % num_jt, j0, col0, valid);
     const long long a0 = (bid / num_jt) * TA;
     const int nchunks = (N + NC - 1) / NC;
     // chunk-local pilot entry t holds p[(c*NC + t - (j0 + TJ - 1)) mod N]
-    const long long eoff = (long long)j0 + TJ - 1;
+    const long long eoff = j0 + TJ - 1;
 
     auto stage = [&](int c, int buf) {
         const int n0 = c * NC;
@@ -84,7 +86,7 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
             const int aa = i / NC, nn = i % NC;
             const long long a = a0 + aa;
             const bool ok = (a < A) && (n0 + nn < N);
-            const float2* src = ok ? (Y + a * N + n0 + nn) : Y;
+            const float2* src = ok ? (Y + a * y_stride + n0 + nn) : Y;
             cp_async8(&sm.y[buf][aa][nn], src, ok);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
@@ -151,19 +153,22 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
     for (int i = 0; i < RA; ++i) {
         const long long a = a0 + warp * RA + i;
         if (a >= A) continue;
-        float2* hrow = H + a * KL;
+        float2* hrow = H + a * lags.ldH + col0;
 #pragma unroll
         for (int r = 0; r < RJ; ++r) {
-            const int j = j0 + RJ * lane + r;
-            if (j < KL) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
+            const int j = RJ * lane + r;
+            if (j < valid) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
         }
     }
 }
 
 template <int MODE>
-cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, long long A,
-                   int N, int KL, int nmod, float2* H, cudaStream_t s) {
-    const int num_jt = (KL + TJ - 1) / TJ;
+cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, long long y_stride,
+                   long long A, int N, const pnce::LagMap& lags, int nmod, float2* H,
+                   cudaStream_t s) {
+    const long long num_jt_ll = pnce::lag_tiles(lags, TJ);
+    if (num_jt_ll > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const int num_jt = (int)num_jt_ll;
     const long long blocks = (long long)num_jt * ((A + TA - 1) / TA);
     if (blocks <= 0) return cudaSuccess;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
@@ -172,8 +177,8 @@ cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, lo
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const float invN = (float)(1.0 / (double)nmod);
-    simt_corr_kernel<MODE><<<(unsigned)blocks, 256, smem, s>>>(bits, preal, Y, A, N, KL, nmod,
-                                                               num_jt, invN, H);
+    simt_corr_kernel<MODE><<<(unsigned)blocks, 256, smem, s>>>(bits, preal, Y, y_stride, A, N,
+                                                               lags, nmod, num_jt, invN, H);
     return cudaGetLastError();
 }
 
@@ -183,20 +188,29 @@ namespace pnce {
 
 cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s) {
-    return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Y, A, N, KL, N, H, s);
+    return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Y, N, A, N, lagmap_contiguous(KL), N,
+                            H, s);
+}
+
+cudaError_t launch_simt_bits_ex(const pnce_pilot* pilot, const float2* Y, long long y_stride,
+                                long long A, int N, const LagMap& lags, float2* H,
+                                cudaStream_t s) {
+    return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Y, y_stride, A, N, lags, N, H, s);
 }
 
 cudaError_t launch_simt_real(const float* p, bool tanh_map, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s) {
-    return tanh_map ? launch<FWD_TANH>(nullptr, p, Y, A, N, KL, N, H, s)
-                    : launch<FWD_REAL>(nullptr, p, Y, A, N, KL, N, H, s);
+    const LagMap lm = lagmap_contiguous(KL);
+    return tanh_map ? launch<FWD_TANH>(nullptr, p, Y, N, A, N, lm, N, H, s)
+                    : launch<FWD_REAL>(nullptr, p, Y, N, A, N, lm, N, H, s);
 }
 
 cudaError_t launch_adjoint_dy(const float* p, bool tanh_map, const float2* G, long long A, int N,
                               int KL, float2* dY, cudaStream_t s) {
     // reduction over the KL lags of G, N outputs per row, pilot read backwards
-    return tanh_map ? launch<ADJ_TANH>(nullptr, p, G, A, KL, N, N, dY, s)
-                    : launch<ADJ_REAL>(nullptr, p, G, A, KL, N, N, dY, s);
+    const LagMap lm = lagmap_contiguous(N);
+    return tanh_map ? launch<ADJ_TANH>(nullptr, p, G, KL, A, KL, lm, N, dY, s)
+                    : launch<ADJ_REAL>(nullptr, p, G, KL, A, KL, lm, N, dY, s);
 }
 
 }  // namespace pnce

@@ -6,7 +6,8 @@
 // A: the quantised received block, rows r = 2a (real) / 2a+1 (imaginary) of antenna a,
 //    staged 128 rows x 128 B per pipeline stage by TMA with the 128-byte swizzle.
 // B: never stored in HBM.  The lag order inside a tile is reversed (tile column i holds
-//    lag j0 + BN - 1 - i), which turns the Toeplitz tile into a Hankel one: the value at
+//    lag j0 + BN - 1 - i, j0 the tile's first lag: k*L-contiguous tiles, or per-transmitter
+//    tiles when the transmitters' cyclic shifts are spread out), which turns the Toeplitz tile into a Hankel one: the value at
 //    (column 8q + r, sample n0 + EPR*t + c) is p[(s + G*(QS*q + TS*t) + r + c) mod N].
 //    Every 8-row x 16-byte core matrix of the canonical no-swizzle K-major layout is then
 //    one of a short list indexed by D = QS*q + TS*t, so the pilot operand of a stage is
@@ -53,7 +54,7 @@ constexpr int EPI_BYTES = 4 * 4096;       // 4 warps x (16 antennas x 32 lags x 
 
 struct TcParams {
     int N;
-    int KL;
+    pnce::LagMap lags;      // which lags each lag tile holds and where they go in H
     long long A;            // antennas
     int BN;                 // lags per tile (multiple of 32, <= 256)
     int num_jt;             // lag blocks
@@ -330,7 +331,9 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     if constexpr (RES) {
         // the CTA's lag block never changes (grid is a multiple of num_jt): build the
         // pilot operand of all its K blocks once
-        const long long j0 = (long long)(blockIdx.x % num_jt) * BN;
+        long long j0;
+        int col0, valid;
+        pnce::lag_tile(prm.lags, BN, blockIdx.x % num_jt, j0, col0, valid);
         gen_pilot_rows<DT>(sB, ext, prm.N, -j0 - BN + 1, prm.res_rows, threadIdx.x, THREADS);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -376,7 +379,9 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
         uint32_t stage = 0, phase = 0;
         bool ok = true;
         for (long long t = blockIdx.x; t < prm.num_tiles && ok; t += gridDim.x) {
-            const long long j0 = (long long)(t % num_jt) * BN;
+            long long j0;
+            int col0, valid;
+            pnce::lag_tile(prm.lags, BN, t % num_jt, j0, col0, valid);
             for (int kb = 0; kb < num_kb; ++kb) {
                 int got = 1;
                 if (lane == 0) got = wait_bar(&ctl->empty[stage], phase ^ 1u, ctl, prm, true);
@@ -444,7 +449,10 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
         uint32_t acc = 0, acc_phase = 0;
         for (long long t = blockIdx.x; t < prm.num_tiles; t += gridDim.x) {
             const long long rb = t / num_jt;
-            const int j0 = (int)(t % num_jt) * BN;
+            long long j0;                       // first lag of the tile (unused here)
+            int col0, valid;                    // first output column, lags kept
+            pnce::lag_tile(prm.lags, BN, t % num_jt, j0, col0, valid);
+            const int ldH = prm.lags.ldH;
             int got = 1;
             if (lane == 0) got = wait_bar(&ctl->tfull[acc], acc_phase, ctl, prm, true);
             got = __shfl_sync(0xffffffffu, got, 0);
@@ -484,7 +492,7 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                         make_float4(re[2 * k], im[2 * k], re[2 * k + 1], im[2 * k + 1]);
                 }
                 __syncwarp();
-                const int jlo = j0 + BN - 32 - 32 * c;
+                const int jlo = BN - 32 - 32 * c;       // tile-local lag of chunk column 31
 #pragma unroll
                 for (int it = 0; it < 8; ++it) {
                     const int row = 2 * it + (lane >> 4), lc = lane & 15;
@@ -492,13 +500,14 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                     const float4 val = stg[row * 16 + pc];
                     const long long ant = ant_base + row;
                     const int j = jlo + 2 * lc;
-                    if (ant < prm.A && j < prm.KL) {
-                        float2* dst = H + ant * prm.KL + j;
-                        if (j + 1 < prm.KL && ((ant * prm.KL) & 1) == 0) {
+                    if (ant < prm.A && j < valid) {
+                        const long long off = ant * ldH + col0;
+                        float2* dst = H + off + j;
+                        if (j + 1 < valid && (off & 1) == 0) {
                             *reinterpret_cast<float4*>(dst) = val;
                         } else {
                             dst[0] = make_float2(val.x, val.y);
-                            if (j + 1 < prm.KL) dst[1] = make_float2(val.z, val.w);
+                            if (j + 1 < valid) dst[1] = make_float2(val.z, val.w);
                         }
                     }
                 }
@@ -544,8 +553,9 @@ unsigned long long wait_limit_ns() {
 }
 
 template <int DT>
-pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N, int KL,
-                      const void* operand, const float* factors, float2* H, cudaStream_t s) {
+pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
+                      const pnce::LagMap& lags, const void* operand, const float* factors,
+                      float2* H, cudaStream_t s) {
     using F = TcFmt<DT>;
     auto enc = encode_fn();
     if (!enc) return PNCE_ECUDA;
@@ -566,11 +576,17 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
 
     TcParams prm;
     prm.N = N;
-    prm.KL = KL;
+    prm.lags = lags;
     prm.A = A;
-    prm.num_jt = (KL + MAX_BN - 1) / MAX_BN;
-    const int per = (KL + prm.num_jt - 1) / prm.num_jt;
+    // lag tile width: as few tiles of <= 256 lags as cover a run, split evenly (a run is
+    // all K*L lags when they are contiguous, one transmitter's L lags otherwise)
+    const int run = lags.mode == 0 ? lags.ldH : lags.L;
+    const int tiles_per_run = (run + MAX_BN - 1) / MAX_BN;
+    const int per = (run + tiles_per_run - 1) / tiles_per_run;
     prm.BN = (per + 31) / 32 * 32;
+    const long long njt = pnce::lag_tiles(lags, prm.BN);
+    if (njt > (1 << 30)) return PNCE_EUNSUPPORTED;
+    prm.num_jt = (int)njt;
     const long long num_rb = (2 * A + BM - 1) / BM;
     prm.num_tiles = num_rb * prm.num_jt;
     prm.num_kb = (N + F::BK - 1) / F::BK;
@@ -619,18 +635,24 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
 
 namespace pnce {
 
+pnce_status launch_tc_ex(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
+                         const LagMap& lm, int dtype, const void* operand, const float* factors,
+                         float2* H, cudaStream_t s) {
+    if (!(h->cc_major == 10 && h->cc_minor == 3)) return PNCE_EUNSUPPORTED;
+    switch (dtype) {
+        case PNCE_FP16: return launch_dt<PNCE_FP16>(h, pilot, A, N, lm, operand, factors, H, s);
+        case PNCE_BF16: return launch_dt<PNCE_BF16>(h, pilot, A, N, lm, operand, factors, H, s);
+        case PNCE_FP8E4M3:
+            return launch_dt<PNCE_FP8E4M3>(h, pilot, A, N, lm, operand, factors, H, s);
+        case PNCE_TF32: return launch_dt<PNCE_TF32>(h, pilot, A, N, lm, operand, factors, H, s);
+        default: return PNCE_EINVAL;
+    }
+}
+
 pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N, int KL,
                       int dtype, const void* operand, const float* factors, float2* H,
                       cudaStream_t s) {
-    if (!(h->cc_major == 10 && h->cc_minor == 3)) return PNCE_EUNSUPPORTED;
-    switch (dtype) {
-        case PNCE_FP16: return launch_dt<PNCE_FP16>(h, pilot, A, N, KL, operand, factors, H, s);
-        case PNCE_BF16: return launch_dt<PNCE_BF16>(h, pilot, A, N, KL, operand, factors, H, s);
-        case PNCE_FP8E4M3:
-            return launch_dt<PNCE_FP8E4M3>(h, pilot, A, N, KL, operand, factors, H, s);
-        case PNCE_TF32: return launch_dt<PNCE_TF32>(h, pilot, A, N, KL, operand, factors, H, s);
-        default: return PNCE_EINVAL;
-    }
+    return launch_tc_ex(h, pilot, A, N, lagmap_contiguous(KL), dtype, operand, factors, H, s);
 }
 
 }  // namespace pnce

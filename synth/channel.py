@@ -93,6 +93,44 @@ def received(h: np.ndarray, bits: np.ndarray, snr_db, rng: np.random.Generator,
     return y.reshape(F, M, N)
 
 
+def shifts_kl(K: int, L: int, N: int) -> np.ndarray:
+    """Cyclic shift of transmitter k: k*L (contiguous lags)."""
+    return np.arange(K) * L
+
+
+def shifts_spread(K: int, L: int, N: int) -> np.ndarray:
+    """Cyclic shift of transmitter k spread evenly over the sequence: k*floor(N/K)."""
+    return np.arange(K) * (N // K)
+
+
+def received_with_cp(h: np.ndarray, bits: np.ndarray, snr_db, rng: np.random.Generator,
+                     cp_len: int, shifts=None, noise: bool = True) -> np.ndarray:
+    """Received blocks of cp_len + N samples, cyclic prefix included (Sec. II-A, Fig. 1).
+
+    Transmitter k sends its cyclically shifted pilot s_k[n] = p[(n - shift_k) mod N] preceded
+    by its last cp_len samples; the channel acts by LINEAR convolution with h[f,m,k,:]; the
+    receiver keeps the first cp_len + N samples.  With L <= cp_len + 1 the samples after
+    the prefix equal the circular model of `received`.
+    """
+    F, M, K, L = h.shape
+    N = bits.size
+    p = mseq.bpsk(bits)
+    sh = shifts_kl(K, L, N) if shifts is None else np.asarray(shifts)
+    T = cp_len + N
+    y = np.zeros((F, M, T), dtype=np.complex128)
+    for k in range(K):
+        s = p[(np.arange(N) - sh[k]) % N]
+        tx = np.concatenate([s[N - cp_len:], s]) if cp_len else s
+        for l in range(L):
+            y[..., l:] += h[..., k, l][..., None] * tx[None, None, : T - l]
+    if noise:
+        snr = np.broadcast_to(np.asarray(snr_db, dtype=np.float64), (F,))
+        sigma = np.sqrt(10.0 ** (-snr / 10.0) / 2.0)[:, None, None]
+        g = rng.standard_normal((F, M, T, 2))
+        y = y + sigma * (g[..., 0] + 1j * g[..., 1])
+    return y.astype(np.complex64)
+
+
 @dataclass(frozen=True)
 class Workload:
     """One synthetic estimation workload (shapes of the paper's sweeps)."""

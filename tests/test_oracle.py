@@ -343,3 +343,42 @@ def test_mae_eq12():
     h = np.array([[[[1, 3 + 4j]]]])
     assert O.mae(est, h) == pytest.approx((1 + 5) / 2)
     assert O.nmse(h, h) == 0.0
+
+
+# ------------------------------------------- cyclic prefix and shift rules (Sec. II)
+
+
+@pytest.mark.parametrize("shift_rule", ["kl", "spread"])
+@pytest.mark.parametrize("r,M,K,L,cp", [(7, 3, 2, 16, 16), (9, 2, 4, 20, 31), (6, 2, 3, 5, 8)])
+def test_cp_linear_channel_closed_form(r, M, K, L, cp, shift_rule):
+    # a LINEAR channel on the CP-prefixed pilot, CP dropped at the receiver, gives the
+    # circular model exactly (Sec. II-A), so the noise-free estimate is h + (h - S)/N
+    bits = S.mseq_bits(r, 2)
+    N = bits.size
+    rng = np.random.default_rng(r)
+    h = C.channel(rng, 2, M, K, L)
+    sh = (C.shifts_kl if shift_rule == "kl" else C.shifts_spread)(K, L, N)
+    Y = C.received_with_cp(h, bits, 0.0, rng, cp, shifts=sh, noise=False)
+    H = O.estimate_general(Y, bits, K, L, cp_len=cp, shifts=sh)
+    x = h.reshape(2, M, K * L)
+    want = (x + (x - x.sum(-1, keepdims=True)) / N).reshape(h.shape)
+    assert np.abs(H - want).max() <= 1e-5 * np.abs(want).max()
+
+
+def test_cp_removal_matches_circular_generator():
+    bits = S.mseq_bits(8, 0)
+    rng = np.random.default_rng(0)
+    h = C.channel(rng, 1, 4, 3, 12)
+    y_cp = C.received_with_cp(h, bits, 0.0, rng, 12, noise=False)
+    y_circ = C.received(h, bits, 0.0, rng, noise=False)
+    assert np.abs(y_cp[..., 12:] - y_circ).max() <= 1e-5
+    # general estimator with cp 0 and k*L shifts is the plain estimator
+    assert np.abs(O.estimate_general(y_circ, bits, 3, 12) - O.estimate(y_circ, bits, 3, 12)).max() <= 1e-12
+
+
+def test_spread_shift_rule_eq8():
+    # Eq. 8: shift of transmitter t = (N / N_batch) * (t mod N_batch), floored
+    assert list(C.shifts_spread(4, 16, 1023)) == [0, 255, 510, 765]
+    with pytest.raises(ValueError):
+        O.estimate_general(np.zeros((1, 1, 7), np.complex64), np.zeros(7, np.uint8), 2, 4,
+                           shifts=[0, 3])          # lags 0..3 and 3..6 overlap
