@@ -205,6 +205,23 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0):
     return res
 
 
+def rank_first_frame(F: int, rank: int, world: int) -> int:
+    """Weak scaling: every rank estimates its own batch of F frames, rank r taking frames
+    [r*F, (r+1)*F) of the synthetic stream (no data crosses ranks)."""
+    return rank * F if world > 1 else 0
+
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time (the whole job finishes with it)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -259,6 +276,8 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=2, help="frames per reference step")
     ap.add_argument("--serving-seconds", type=float, default=1.0,
                     help="length of the Poisson serving trace (0: skip)")
+    ap.add_argument("--other-dtypes", type=int, default=1,
+                    help="also time the other arithmetics on the same batch (1/0)")
     args = ap.parse_args()
 
     w = C.WORKLOADS[args.workload]
@@ -287,7 +306,7 @@ def main():
             dist.barrier()
 
     # ---- inputs (each rank its own batch: frames offset by rank)
-    bits, Y_host = C.make_received(w, first=rank * w.F if world > 1 else 0)
+    bits, Y_host = C.make_received(w, first=rank_first_frame(w.F, rank, world))
     Y_pin = torch.from_numpy(Y_host).pin_memory()
     Y = Y_pin.to(dev)
     F, M, N, K, L = w.F, w.M, w.N, w.K, w.L
@@ -328,11 +347,7 @@ def main():
     clk = clocks.stop()
     trace = pk.trace_read(dev)       # (kind, ms) of every kernel launched in the timed region
     pk.trace_enable(False, dev)
-    total_ms = e_start.elapsed_time(e_end)
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(e_start.elapsed_time(e_end), world, dev)
     assert pk.get_status(dev) == 0
     main_kind = "simt" if dt == "fp32" else "correlate"
     corr_ms = [ms for kind, ms in trace if kind == main_kind]
@@ -373,11 +388,7 @@ def main():
                                     H_pin.data_ptr(), stream.cuda_stream)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
     e2e_value = taps_per_step * args.e2e_steps * world / (e2e_ms / 1e3)
     assert pk.get_status(dev) == 0
     e2e_matches = bool(torch.equal(H_pin, H.cpu()))
@@ -430,6 +441,27 @@ def main():
 
     serving = run_serving(dev, args.serving_seconds) if args.serving_seconds > 0 else None
 
+    # the other arithmetics on the same batch (shorter runs, same step definition)
+    others = {}
+    if args.other_dtypes:
+        for odt in [d for d in ("e4m3", "bf16", "tf32", "fp16", "fp32") if d != dt]:
+            ows = (torch.empty(pk.workspace_size(F, M, N, K, L, odt), dtype=torch.uint8,
+                               device=dev) if odt != "fp32" else None)
+            for _ in range(3):
+                pk.estimate(Y, pilot, K, L, dtype=odt, out=H, workspace=ows)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            n_o = 50 if odt != "fp32" else 5
+            a0.record(stream)
+            for _ in range(n_o):
+                pk.estimate(Y, pilot, K, L, dtype=odt, out=H, workspace=ows)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms_o = a0.elapsed_time(a1) / n_o
+            others[odt] = {"ms_per_step": ms_o, "value": taps_per_step / (ms_o / 1e3)}
+            del ows
+        assert pk.get_status(dev) == 0
+
     line = {
         "metric": "CIR taps estimated/s", "value": value, "unit": "taps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -452,6 +484,7 @@ def main():
         "nmse_vs_oracle": nmse,
         "cpu_baseline": cpu,
         "serving": serving,
+        "other_dtypes": others,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
