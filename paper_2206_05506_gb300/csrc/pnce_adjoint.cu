@@ -12,9 +12,7 @@
 // shared buffers.  A lane's 8 outputs read Y at consecutive offsets, so a 15-entry
 // register window slides along the staged row.  The 8 warps' sums are added in a fixed
 // order and written as one partial row per antenna group; a second kernel adds the
-// partial rows in a fixed order.  The result is bitwise reproducible.  The real-part and
-// imaginary-part products accumulate in the two lanes of one packed FMA (fma.rn.f32x2)
-// and are added when the warp's sums are combined.
+// partial rows in a fixed order.  The result is bitwise reproducible.
 #include "pnce_internal.h"
 
 namespace {
@@ -33,17 +31,6 @@ struct WarpBuf {
     float2 g[JC];
 };
 
-typedef unsigned long long u64;
-
-__device__ __forceinline__ void ffma2(u64& acc, u64 a, u64 b) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(a), "l"(b));
-}
-__device__ __forceinline__ float lanesum(u64 v) {
-    float x, y;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
-    return x + y;
-}
-
 __global__ void __launch_bounds__(256)
 dp_partial_kernel(const float2* __restrict__ G, const float2* __restrict__ Y, long long A, int N,
                   int KL, int num_qt, float* __restrict__ partial, int pitch) {
@@ -56,9 +43,9 @@ dp_partial_kernel(const float2* __restrict__ G, const float2* __restrict__ Y, lo
     const long long a_end = min(A, a_begin + AGROUP);
     WarpBuf& B = wb[warp];
 
-    u64 acc[8];                      // (sum of re*re, sum of im*im) per output
+    float acc[8];
 #pragma unroll
-    for (int r = 0; r < 8; ++r) acc[r] = 0ull;
+    for (int r = 0; r < 8; ++r) acc[r] = 0.f;
 
     for (long long a = a_begin + warp; a < a_end; a += 8) {
         const float2* yrow = Y + a * N;
@@ -77,22 +64,23 @@ dp_partial_kernel(const float2* __restrict__ G, const float2* __restrict__ Y, lo
             __syncwarp();
             // output q0 + 8*lane + r at lag j0 + u reads entry 8*lane + r + u
             const int base = 8 * lane;
-            const u64* wv = reinterpret_cast<const u64*>(B.w);
-            const u64* gv = reinterpret_cast<const u64*>(B.g);
-            u64 w[15];
+            float2 w[15];
 #pragma unroll
-            for (int i = 0; i < 15; ++i) w[i] = wv[wpos(base + i)];
+            for (int i = 0; i < 15; ++i) w[i] = B.w[wpos(base + i)];
             const int nblk = min(JC, KL - j0 + 7) / 8;
 #pragma unroll 1
             for (int s = 0; s < nblk; ++s) {
-                u64 nw[8];
+                float2 nw[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) nw[i] = wv[wpos(base + 8 * s + 15 + i)];
+                for (int i = 0; i < 8; ++i) nw[i] = B.w[wpos(base + 8 * s + 15 + i)];
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
-                    const u64 g = gv[8 * s + u];
+                    const float2 g = B.g[8 * s + u];
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) ffma2(acc[r], g, w[u + r]);
+                    for (int r = 0; r < 8; ++r) {
+                        acc[r] = fmaf(g.x, w[u + r].x, acc[r]);
+                        acc[r] = fmaf(g.y, w[u + r].y, acc[r]);
+                    }
                 }
 #pragma unroll
                 for (int i = 0; i < 7; ++i) w[i] = w[i + 8];
@@ -102,7 +90,7 @@ dp_partial_kernel(const float2* __restrict__ G, const float2* __restrict__ Y, lo
         }
     }
 #pragma unroll
-    for (int r = 0; r < 8; ++r) red[warp][8 * lane + r] = lanesum(acc[r]);
+    for (int r = 0; r < 8; ++r) red[warp][8 * lane + r] = acc[r];
     __syncthreads();
     for (int q = tid; q < QT; q += 256) {
         float s = 0.f;

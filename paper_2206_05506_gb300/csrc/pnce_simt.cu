@@ -6,9 +6,7 @@
 // pilot[(k - o) mod Nmod], o < Nout.
 //
 // Block tile: 32 antennas x 256 lags; thread tile: 4 antennas x 8 consecutive lags, so
-// each received sample read from shared memory feeds 64 FMAs.  The real and imaginary
-// parts of a sample share the same pilot factor, so every update is one packed two-lane
-// FMA (fma.rn.f32x2) on a (re, im) register pair: half the issue slots of scalar FMAs.  Because a thread's lags
+// each received sample read from shared memory feeds 64 FMAs.  Because a thread's lags
 // are consecutive, the pilot values it needs at sample n+1 are those of sample n shifted
 // by one lag: a 15-entry register window slides along the pilot, one new shared load per
 // sample.  Received samples and the pilot window of each 128-sample chunk are staged in
@@ -44,24 +42,6 @@ struct Smem {
     float e[2][EPAD];
     float2 y[2][TA][NC];
 };
-
-typedef unsigned long long u64;
-
-// (v, v) in one 64-bit register pair
-__device__ __forceinline__ u64 dup2(float v) {
-    u64 r;
-    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(v));
-    return r;
-}
-// acc.(x, y) += p * y.(x, y), both lanes in one instruction
-__device__ __forceinline__ void ffma2(u64& acc, u64 p2, u64 y) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(p2), "l"(y));
-}
-__device__ __forceinline__ float2 unpack2(u64 v) {
-    float2 r;
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
-    return r;
-}
 
 // FWD_BITS: +-1 pilot from packed bits.  FWD_REAL / ADJ_REAL: float pilot, read forwards
 // or backwards.  *_TANH: the float argument is theta and the pilot is tanh(theta).
@@ -117,11 +97,11 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
         }
     };
 
-    u64 acc[RA][RJ];
+    float2 acc[RA][RJ];
 #pragma unroll
     for (int i = 0; i < RA; ++i)
 #pragma unroll
-        for (int r = 0; r < RJ; ++r) acc[i][r] = 0ull;
+        for (int r = 0; r < RJ; ++r) acc[i][r] = make_float2(0.f, 0.f);
 
     // lag of (lane, r) is j0 + 8*lane + r; chunk-local entry for sample n0+u is
     // u + base - r with base = TJ - 1 - 8*lane (>= 7)
@@ -136,31 +116,34 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
         if (c + 1 < nchunks) stage(c + 1, buf ^ 1);
 
         const float* e = sm.e[buf];
-        const u64* yrow[RA];
+        float w[15];
 #pragma unroll
-        for (int i = 0; i < RA; ++i)
-            yrow[i] = reinterpret_cast<const u64*>(&sm.y[buf][warp * RA + i][0]);
-        u64 w[15];                                 // pilot window, each value duplicated
-#pragma unroll
-        for (int i = 0; i < 15; ++i) w[i] = dup2(e[epos(base - 7 + i)]);
+        for (int i = 0; i < 15; ++i) w[i] = e[epos(base - 7 + i)];
 
 #pragma unroll 1
         for (int s = 0; s < NC / 8; ++s) {
+            float nw[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) nw[i] = e[epos(8 * s + 8 + base + i)];
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                u64 y[RA];
+                float2 y[RA];
 #pragma unroll
-                for (int i = 0; i < RA; ++i) y[i] = yrow[i][8 * s + u];
+                for (int i = 0; i < RA; ++i) y[i] = sm.y[buf][warp * RA + i][8 * s + u];
 #pragma unroll
                 for (int r = 0; r < RJ; ++r) {
+                    const float pv = w[u - r + 7];
 #pragma unroll
-                    for (int i = 0; i < RA; ++i) ffma2(acc[i][r], w[u - r + 7], y[i]);
+                    for (int i = 0; i < RA; ++i) {
+                        acc[i][r].x = fmaf(pv, y[i].x, acc[i][r].x);
+                        acc[i][r].y = fmaf(pv, y[i].y, acc[i][r].y);
+                    }
                 }
             }
 #pragma unroll
             for (int i = 0; i < 7; ++i) w[i] = w[i + 8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) w[7 + i] = dup2(e[epos(8 * s + 8 + base + i)]);
+            for (int i = 0; i < 8; ++i) w[7 + i] = nw[i];
         }
         cp_async_wait_all();
         __syncthreads();
@@ -174,10 +157,7 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
 #pragma unroll
         for (int r = 0; r < RJ; ++r) {
             const int j = RJ * lane + r;
-            if (j < valid) {
-                const float2 v = unpack2(acc[i][r]);
-                hrow[j] = make_float2(v.x * invN, v.y * invN);
-            }
+            if (j < valid) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
         }
     }
 }
