@@ -23,6 +23,10 @@
  *    Calls only enqueue work; results are ready when the stream reaches them.
  *  - Every function returns a pnce_status and never aborts or prints.  Arguments are
  *    validated before anything is launched; an invalid call launches nothing.
+ *  - A handle may be used from several host threads: the sections that enqueue work on
+ *    the handle's own streams (large-batch overlap in pnce_estimate, pnce_estimate_host)
+ *    and the trace record are serialised inside the library.  Such sections of different
+ *    calls then also run one after the other on the GPU.
  *    Errors raised on the device after launch (a bounded wait that ran out inside a
  *    kernel) are latched in the handle and reported by pnce_get_status().
  *  - Shape rules: F, M >= 1; N >= 2; K, L >= 1 and K*L <= N (Eq. 7 with C = L: the
@@ -197,7 +201,7 @@ pnce_status pnce_backward(pnce_handle* h, const float* pilot_dev, int pilot_map,
  * end: to the caller the call behaves as if it were enqueued on `stream`.  All device
  * buffers live in workspace_dev (pnce_host_workspace_size bytes, caller-owned).  Host
  * buffers should be page-locked for the copies to be asynchronous.  Calls on the same
- * handle must not overlap in time (they share the handle's pipeline streams).
+ * handle are serialised on the handle's pipeline streams.
  */
 size_t pnce_host_workspace_size(int F, int M, int N, int K, int L, int dtype);
 pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const void* Y_host,

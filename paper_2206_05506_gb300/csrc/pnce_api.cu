@@ -64,6 +64,7 @@ int estimate_chunks(const pnce_handle* h, int F, int M, int N, int KL) {
 pnce_status estimate_overlapped(pnce_handle* h, const pnce_pilot* pilot, const float2* Y, int F,
                                 int M, int N, int KL, int dtype, void* ws, float2* H,
                                 cudaStream_t user, int nch) {
+    std::lock_guard<std::recursive_mutex> guard(h->lock);   // uses the handle's streams
     const long long A = (long long)F * M;
     const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
     unsigned char* operand = static_cast<unsigned char*>(pnce::ws_operand(ws, lay));
@@ -200,6 +201,7 @@ pnce_status pnce_destroy(pnce_handle* h) {
 
 pnce_status pnce_trace_enable(pnce_handle* h, int on) {
     if (!h) return PNCE_EINVAL;
+    std::lock_guard<std::recursive_mutex> guard(h->lock);
     if (on && !h->trace_ev) {
         pnce_status st = check_device(h);
         if (st != PNCE_OK) return st;
@@ -218,6 +220,7 @@ pnce_status pnce_trace_read(pnce_handle* h, int* kinds, float* ms, int max_entri
     if (!h || !count || max_entries < 0 || (max_entries > 0 && (!kinds || !ms)))
         return PNCE_EINVAL;
     *count = 0;
+    std::lock_guard<std::recursive_mutex> guard(h->lock);
     if (!h->trace_ev) return PNCE_OK;
     const int n = h->trace_n < max_entries ? h->trace_n : max_entries;
     for (int i = 0; i < n; ++i) {
@@ -520,6 +523,7 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
     if (dtype != PNCE_FP32_SIMT && !(h->cc_major == 10 && h->cc_minor == 3))
         return PNCE_EUNSUPPORTED;
 
+    std::lock_guard<std::recursive_mutex> guard(h->lock);   // uses the handle's streams
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(workspace_dev);
     const unsigned char* yh = static_cast<const unsigned char*>(Y_host);

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "pnce.h"
 
 struct pnce_handle {
@@ -27,6 +29,9 @@ struct pnce_handle {
     int trace_n;
     cudaEvent_t* trace_ev;              // 2 * kTraceMax events, created on first enable
     int* trace_kind;
+    // serialises the host-side enqueue of the sections that use the handle's own streams,
+    // events or trace record, so calls from several threads cannot interleave them
+    std::recursive_mutex lock;
 };
 
 namespace pnce {
@@ -38,10 +43,13 @@ struct TraceScope {
     cudaStream_t s;
     int slot;
     TraceScope(pnce_handle* h_, cudaStream_t s_, int kind) : h(h_), s(s_), slot(-1) {
-        if (h && h->trace_on && h->trace_n < kTraceMax) {
-            slot = h->trace_n++;
-            h->trace_kind[slot] = kind;
-            cudaEventRecord(h->trace_ev[2 * slot], s);
+        if (h && h->trace_on) {
+            std::lock_guard<std::recursive_mutex> g(h->lock);
+            if (h->trace_n < kTraceMax) {
+                slot = h->trace_n++;
+                h->trace_kind[slot] = kind;
+                cudaEventRecord(h->trace_ev[2 * slot], s);
+            }
         }
     }
     ~TraceScope() {
