@@ -151,9 +151,10 @@ def cpu_oracle_sample(bits, Y_sample, K, L, target_s=15.0, max_frames=None):
     """Time the FP64 oracle on a growing prefix of frames until about target_s of work."""
     from oracle import pn_oracle as O
 
+    O.estimate(Y_sample[:1], bits, K, L)                      # warm (BLAS threads, caches)
     t0 = time.perf_counter()
-    O.estimate(Y_sample[:1], bits, K, L)
-    t1 = time.perf_counter() - t0
+    O.estimate(Y_sample[:2], bits, K, L)
+    t1 = (time.perf_counter() - t0) / 2
     nf = int(max(1, min(Y_sample.shape[0], (max_frames or 10 ** 9), round(target_s / max(t1, 1e-3)))))
     t0 = time.perf_counter()
     H = O.estimate(Y_sample[:nf], bits, K, L)
