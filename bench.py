@@ -1,9 +1,7 @@
 """Benchmark: PN-correlation channel estimation throughput on GB300.
 
 One step = one pnce_estimate call over one batch: per-antenna quantisation of the
-received blocks and the tensor-core correlation with its epilogue (for a batch this large
-the library overlaps the quantisation of frame chunk i+1 with the correlation of chunk i),
-on synthetic received blocks shaped like the precision workload (M=128 antennas, N=4095
+received blocks, then the tensor-core correlation with its epilogue, on synthetic received blocks shaped like the precision workload (M=128 antennas, N=4095
 m-sequence, K=16 transmitters x L=128 taps, 512 frames, SNR 0/10/20/30 dB), inputs
 resident in HBM.  The library's tracing records CUDA events around each kernel it
 launches, on the stream the kernel runs on; the correlation kernels' durations give the
@@ -223,6 +221,47 @@ def max_over_ranks(ms: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def run_differentiation(dev, steps: int = 20):
+    """Relaxed-pilot forward + adjoint (dLoss/dY and dLoss/dtheta) on the differentiation
+    workload (M=64, N=1023, K=8, L=64, 64 frames, FP32), as one training step would."""
+    import torch
+
+    import paper_2206_05506_gb300 as pk
+    from paper_2206_05506_gb300.autograd import relaxed_estimate
+
+    w = C.DIFFERENTIATION
+    bits, h, Y = C.make(w)
+    Yd = torch.from_numpy(Y).to(dev).requires_grad_(True)
+    Ht = torch.from_numpy(h.astype(np.complex64)).to(dev)
+    theta = torch.randn(w.N, device=dev, generator=torch.Generator(dev).manual_seed(0))
+    theta.requires_grad_(True)
+
+    def step():
+        Yd.grad = None
+        theta.grad = None
+        loss = (relaxed_estimate(Yd, theta, w.K, w.L) - Ht).abs().pow(2).mean()
+        loss.backward()
+        return loss
+
+    for _ in range(3):
+        step()
+    pk.trace_enable(True, dev)
+    pk.trace_read(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    pk.trace_enable(False, dev)
+    ms = e0.elapsed_time(e1) / steps
+    fl = 4.0 * w.F * w.M * w.N * w.K * w.L          # one correlation-sized pass
+    return {"workload": w.name, "ms_per_step": ms,
+            "forward_plus_adjoint_tflops": 3 * fl / (ms / 1e3) / 1e12,
+            "note": "loss and its torch elementwise ops included; 3 correlation-sized passes"}
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -277,6 +316,8 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=2, help="frames per reference step")
     ap.add_argument("--serving-seconds", type=float, default=1.0,
                     help="length of the Poisson serving trace (0: skip)")
+    ap.add_argument("--differentiation", type=int, default=1,
+                    help="also time the relaxed-pilot forward + adjoint (1/0)")
     ap.add_argument("--other-dtypes", type=int, default=1,
                     help="also time the other arithmetics on the same batch (1/0)")
     args = ap.parse_args()
@@ -320,8 +361,7 @@ def main():
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        # the product call: pnce_estimate; for large batches it overlaps the quantisation of
-        # frame chunk i+1 with the tensor-core correlation of chunk i on internal streams
+        # the product call (quantise, then correlate; PNCE_OVERLAP_CHUNKS would overlap them)
         pk.estimate(Y, pilot, K, L, dtype=dt, out=H, workspace=ws)
 
     pk.trace_enable(True, dev)
@@ -441,6 +481,7 @@ def main():
         nmse = O.nmse(H[:nf].cpu().numpy(), Href)
 
     serving = run_serving(dev, args.serving_seconds) if args.serving_seconds > 0 else None
+    differentiation = run_differentiation(dev) if args.differentiation else None
 
     # the other arithmetics on the same batch (shorter runs, same step definition)
     others = {}
@@ -486,6 +527,7 @@ def main():
         "cpu_baseline": cpu,
         "serving": serving,
         "other_dtypes": others,
+        "differentiation": differentiation,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

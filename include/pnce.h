@@ -100,7 +100,10 @@ size_t pnce_workspace_size(int F, int M, int N, int K, int L, int dtype);
  * Y_dev: complex64 [F][M][N]; H_dev: complex64 [F][M][K][L] (fully overwritten).
  * dtype: a pnce_dtype.  For the tensor-core dtypes Y is first quantised per antenna
  * (pnce_quantize) into workspace_dev, then correlated on the tensor cores; the FP32 SIMT
- * path ignores the workspace (may be NULL).
+ * path ignores the workspace (may be NULL).  With the environment variable
+ * PNCE_OVERLAP_CHUNKS=n (2..8), a large tensor-core batch is cut into n frame chunks whose
+ * quantisation overlaps the previous chunk's correlation on the handle's own streams
+ * (the call still behaves as if enqueued on `stream`); by default the two run in order.
  */
 pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y_dev,
                           int F, int M, int N, int K, int L, int dtype,

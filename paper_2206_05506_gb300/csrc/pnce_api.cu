@@ -37,26 +37,24 @@ pnce_status check_device(const pnce_handle* h) {
 
 pnce_status from_cuda(cudaError_t e) { return e == cudaSuccess ? PNCE_OK : PNCE_ECUDA; }
 
-// Frame chunks for pnce_estimate: a large batch is quantised chunk by chunk on one stream
-// while the tensor-core kernel correlates the previous chunk on another (the quantiser is
-// HBM-bound, the correlation tensor-bound, and their blocks fit on an SM together).  Each
-// chunk keeps >= 8 waves of 128 x 256 tiles so the per-launch tail stays small.
-// Quantiser grid while it overlaps a correlation: PNCE_QUANT_BLOCKS_PER_SM blocks per SM,
-// default 0 = one block per antenna (measured on GB300, 512 x 128 x 4095 fp16: 1.65 ms per
-// estimate uncapped, 1.96 / 1.73 / 1.67 ms with 1 / 2 / 4 blocks per SM).
-int quant_blocks_overlapped(const pnce_handle* h) {
-    const char* e = getenv("PNCE_QUANT_BLOCKS_PER_SM");
-    const int per = e ? atoi(e) : 0;
-    return per > 0 ? per * h->num_sms : 0;
-}
-
+// Frame chunks for pnce_estimate.  Off by default: the quantiser of a batch runs, then the
+// tensor-core correlation.  PNCE_OVERLAP_CHUNKS=n (2..8) splits a large batch into n frame
+// chunks and quantises chunk i+1 on one handle stream while chunk i is correlated on
+// another.  Measured on GB300 (512 x 128 x 4095, fp16): 1.716 ms per estimate sequential,
+// 1.743 / 1.653 / 1.650 / 1.798 / 1.691 ms with 2 / 3 / 4 / 6 / 8 chunks -- the quantiser
+// and the correlation compete for the SMs' L1/shared-memory data path, so overlapping buys
+// at most 4 %, and only when each chunk keeps >= 8 waves of 128 x 256 tiles.
 int estimate_chunks(const pnce_handle* h, int F, int M, int N, int KL) {
     (void)N;
+    const char* e = getenv("PNCE_OVERLAP_CHUNKS");
+    long long n = e ? atoll(e) : 1;
+    if (n <= 1) return 1;
+    if (n > 8) n = 8;
     const long long row_blocks_per_frame = (2LL * M + 127) / 128;
     const long long jt = (KL + 255) / 256;
     const long long tiles = (long long)F * row_blocks_per_frame * jt;
-    long long n = tiles / (8LL * h->num_sms);
-    if (n > 4) n = 4;
+    const long long most = tiles / (8LL * h->num_sms);       // chunks of >= 8 waves
+    if (n > most) n = most;
     if (n > F) n = F;
     return n < 2 ? 1 : (int)n;
 }

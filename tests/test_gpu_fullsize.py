@@ -1,7 +1,7 @@
 """Parity at the full precision workload (512 frames x 128 antennas, N = 4095, K = 16,
-L = 128), in the launch configuration the benchmark times: pnce_estimate splits the batch
-into frame chunks whose quantisation overlaps the previous chunk's correlation.  The oracle
-checks sampled frames one by one; per-antenna scales are checked for every antenna."""
+L = 128), in the launch configuration the benchmark times (pnce_estimate: quantise, then
+correlate), and with the optional chunked overlap of the two.  The oracle checks sampled
+frames one by one; per-antenna scales are checked for every antenna."""
 import numpy as np
 import pytest
 import torch
@@ -43,11 +43,14 @@ def test_full_size_sampled_frames(full, dtype):
     assert np.isfinite(p) and 0.5 * w.K < p < 2.0 * w.K
 
 
+@pytest.mark.parametrize("chunks", ["2", "4", "8"])
 @pytest.mark.parametrize("dtype", ["fp16", "e4m3"])
-def test_overlapped_equals_sequential(full, dtype):
+def test_overlapped_equals_sequential(full, dtype, chunks, monkeypatch):
     # the chunked, overlapped pnce_estimate gives the same bits as quantise-then-correlate
     pk, w, bits, Y, Yd, pilot = full
+    monkeypatch.setenv("PNCE_OVERLAP_CHUNKS", chunks)
     H = pk.estimate(Yd, pilot, w.K, w.L, dtype=dtype)
+    monkeypatch.delenv("PNCE_OVERLAP_CHUNKS")
     q = pk.quantize(Yd, dtype)
     H2 = pk.correlate_quantized(q["workspace"], pilot, w.F, w.M, w.K, w.L, dtype)
     assert torch.equal(H, H2)
