@@ -86,7 +86,7 @@ pnce_status estimate_overlapped(pnce_handle* h, const pnce_pilot* pilot, const f
         {
             pnce::TraceScope tr(h, h->s_quant, pnce::TRACE_QUANTIZE);
             e = pnce::launch_quantize(Y + a0 * N, ac, N, dtype, op, fa, nullptr, nullptr,
-                                      h->s_quant, i == 0 ? 0 : quant_blocks_overlapped(h));
+                                      h->s_quant);
         }
         if (e != cudaSuccess || cudaEventRecord(h->ev_q[i], h->s_quant) != cudaSuccess ||
             cudaStreamWaitEvent(h->s_corr, h->ev_q[i], 0) != cudaSuccess)
