@@ -74,3 +74,25 @@ def test_null_arguments_rejected_without_device(lib):
     assert lib.pnce_estimate(None, None, None, 1, 1, 7, 1, 1, 0, None, 0, None, None) == 1
     assert lib.pnce_backward(None, None, 0, None, None, 1, 1, 7, 1, 1, None, None, None, 0,
                              None) == 1
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no CPU or PyTorch fallback: without the built library the binding refuses to run
+    from paper_2206_05506_gb300 import _lib
+    saved = _lib._lib
+    try:
+        _lib._lib = None
+        with pytest.raises(RuntimeError, match="libpnce.so not found"):
+            _lib.load(str(tmp_path / "libpnce.so"))
+    finally:
+        _lib._lib = saved
+
+
+def test_product_code_does_not_import_the_oracle():
+    # the oracle is test infrastructure: nothing under the package may import it
+    pkg = os.path.join(ROOT, "paper_2206_05506_gb300")
+    pat = re.compile(r"^\s*(import|from)\s+oracle\b", re.M)
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith(".py"):
+                assert not pat.search(open(os.path.join(dirpath, f)).read()), f
