@@ -313,7 +313,7 @@ def main():
     ap.add_argument("--frames", type=int, default=None, help="override frames per step")
     ap.add_argument("--e2e-steps", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--ref-frames", type=int, default=2, help="frames per reference step")
+    ap.add_argument("--ref-frames", type=int, default=8, help="frames per reference step")
     ap.add_argument("--serving-seconds", type=float, default=1.0,
                     help="length of the Poisson serving trace (0: skip)")
     ap.add_argument("--differentiation", type=int, default=1,
@@ -421,15 +421,22 @@ def main():
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    per_step = []
     torch.cuda.synchronize()
     e0.record(stream)
     for _ in range(args.e2e_steps):
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
         pk.lib().pnce_estimate_host(pilot.ctx.handle, pilot.handle, Y_pin.data_ptr(), F, M, N, K,
                                     L, pk.DTYPES[dt], hws.data_ptr(), hws.numel(),
                                     H_pin.data_ptr(), stream.cuda_stream)
+        s1.record(stream)
+        per_step.append((s0, s1))
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    e2e_med_ms = max_over_ranks(float(np.median([a.elapsed_time(b) for a, b in per_step])), world, dev)
     e2e_value = taps_per_step * args.e2e_steps * world / (e2e_ms / 1e3)
     assert pk.get_status(dev) == 0
     e2e_matches = bool(torch.equal(H_pin, H.cpu()))
@@ -520,7 +527,12 @@ def main():
         "e2e": {"value": e2e_value, "unit": "taps/s",
                 "h2d_bytes_per_step": int(Y_pin.numel() * 8),
                 "d2h_bytes_per_step": int(H_pin.numel() * 8),
-                "ms_per_step": e2e_ms / args.e2e_steps, "matches_device_result": e2e_matches},
+                "ms_per_step": e2e_ms / args.e2e_steps,
+                "ms_per_step_median": e2e_med_ms,
+                "value_from_median_step": taps_per_step * world / (e2e_med_ms / 1e3),
+                "note": "copy-bound over the host link (~211 GB/s H2D measured); the host "
+                        "is shared, so step times vary between runs",
+                "matches_device_result": e2e_matches},
         "gpu_launches": launches,
         "clocks": clk,
         "nmse_vs_oracle": nmse,
