@@ -130,26 +130,39 @@ __device__ __forceinline__ void mbar_arrive_tx(unsigned long long* b, uint32_t b
                  "r"(bytes)
                  : "memory");
 }
+// CL: acquire at cluster scope, for phases completed by arrivals from the peer CTA
+template <bool CL = false>
 __device__ __forceinline__ bool mbar_test(unsigned long long* b, uint32_t parity) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
+    if constexpr (CL) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(su32(b)), "r"(parity)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.b32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(su32(b)), "r"(parity)
+            : "memory");
+    }
     return ok != 0;
 }
 
 // Bounded wait for the phase of parity `parity` of barrier b.  honor_abort: give up as
 // soon as another role has latched an abort.  Returns false when the wait was abandoned.
+template <bool CL = false>
 __device__ __noinline__ bool wait_bar(unsigned long long* b, uint32_t parity, Ctl* ctl,
                                       const TcParams& prm, bool honor_abort) {
-    if (mbar_test(b, parity)) return true;
+    if (mbar_test<CL>(b, parity)) return true;
     const unsigned long long t0 = gtime();
     for (;;) {
-        if (mbar_test(b, parity)) return true;
+        if (mbar_test<CL>(b, parity)) return true;
         if (honor_abort && *(volatile int*)&ctl->abort_flag) return false;
         if (gtime() - t0 > prm.wait_limit_ns) {
             *(volatile int*)&ctl->abort_flag = 1;
@@ -528,6 +541,332 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     }
 }
 
+// ------------------------------------------------ 2-SM variant (CTA pairs, opt-in)
+//
+// tcgen05.mma.cta_group::2 over a cluster of two CTAs: the pair computes a 256-row x BN-lag
+// tile; each CTA stages its own 128 operand rows and holds the pilot list of its half of
+// the BN lags (rank 0: tile columns [0, BN/2), rank 1: [BN/2, BN)), so each SM reads half
+// the pilot operand per MMA.  Rank 0 issues the MMAs for both; the operand loads of both
+// CTAs complete on rank 0's stage barrier, its commits arrive on the barriers of both CTAs
+// (multicast), and each CTA drains its own 128 accumulator rows, the odd CTA releasing
+// rank 0's accumulator barrier remotely.
+
+struct PairCtl {
+    unsigned long long full_a[STAGES];
+    unsigned long long unused[STAGES];      // keeps the layout of Ctl
+    unsigned long long empty[STAGES];
+    unsigned long long tfull[2];
+    unsigned long long tempty[2];           // rank 0: 4 local + 4 remote epilogue warps
+    uint32_t tmem_base;
+    int abort_flag;
+};
+// same layout as Ctl, so that wait_bar's abort flag is the pair's
+static_assert(sizeof(PairCtl) == sizeof(Ctl) && offsetof(PairCtl, abort_flag) == offsetof(Ctl, abort_flag),
+              "control block layout");
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+// arrive on the barrier at the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ void mbar_arrive_remote(unsigned long long* local, uint32_t rank) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(su32(local)), "r"(rank));
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
+                 : "memory");
+}
+// commit the issuing thread's MMAs to the barrier at this offset in both CTAs of the pair
+__device__ __forceinline__ void umma_commit_pair(unsigned long long* bar) {
+    const uint16_t mask = 3;
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(su32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
+// TMA load into this CTA's shared memory whose completion is counted on the barrier at
+// shared::cluster address `bar_cluster`, which may belong to the peer CTA of the pair
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int x, int y,
+                                                 uint32_t bar_cluster) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_addr(const void* local, uint32_t rank) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(su32(local)), "r"(rank));
+    return remote;
+}
+
+template <int DT>
+__device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t accumulate) {
+    if constexpr (DT == PNCE_FP16 || DT == PNCE_BF16) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else if constexpr (DT == PNCE_TF32) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+template <int DT>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
+               const float* __restrict__ row_scale, float2* __restrict__ H, const TcParams prm) {
+    using F = TcFmt<DT>;
+    constexpr int KSTEPS = 4;
+    constexpr uint32_t LBO = 128u * F::TS, SBO = 128u * F::QS;
+    constexpr uint32_t KSTEP_B = 2u * 128u * F::TS;
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int nst = prm.stages;
+    unsigned char* sA = base;
+    unsigned char* sB = sA + nst * A_STAGE;
+    float4* sEpi = reinterpret_cast<float4*>(sB + prm.b_region);
+    PairCtl* ctl = reinterpret_cast<PairCtl*>(reinterpret_cast<unsigned char*>(sEpi) + EPI_BYTES);
+    Ctl* wctl = reinterpret_cast<Ctl*>(ctl);    // abort flag shared with wait_bar
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int BN = prm.BN, num_jt = prm.num_jt, num_kb = prm.num_kb;
+    const uint32_t rank = cluster_rank();
+    const long long pair = cluster_id(), npairs = cluster_count();
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&ctl->full_a[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl->tfull[b], 1);
+            mbar_init(&ctl->tempty[b], 8);
+        }
+        ctl->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
+                     : "memory");
+    }
+    {
+        // this CTA's half of the pair's lag block: rank 0 the later lags (tile columns
+        // [0, BN/2)), rank 1 the earlier ones; the pair keeps its lag block throughout
+        long long j0;
+        int col0, valid;
+        pnce::lag_tile(prm.lags, BN, pair % num_jt, j0, col0, valid);
+        const int bnc = BN / 2;
+        const long long origin = j0 + (rank == 0 ? bnc : 0);
+        gen_pilot_rows<DT>(sB, ext, prm.N, -origin - bnc + 1, prm.res_rows, threadIdx.x, THREADS);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&ctl->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync_all();      // barriers of both CTAs initialised, both pilot halves built
+    fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+
+    if (warp == 0) {
+        // ------------------------------------------------- TMA producer (both CTAs)
+        // both CTAs' loads of a stage complete on rank 0's full_a, which expects the bytes
+        // of both; each CTA refills a stage when the pair's MMAs have released it (the
+        // commit arrives on the empty barriers of both CTAs)
+        if (lane == 0) {
+            const uint32_t full0 = cluster_addr(&ctl->full_a[0], 0);
+            uint32_t stage = 0, phase = 0;
+            long long issued = 0;
+            bool ok = true;
+            for (long long t = pair; t < prm.num_tiles && ok; t += npairs) {
+                const int y = (int)(2 * (t / num_jt) + rank) * BM;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!wait_bar(&ctl->empty[stage], phase ^ 1u, wctl, prm, true)) {
+                        ok = false;
+                        break;
+                    }
+                    if (rank == 0) mbar_arrive_tx(&ctl->full_a[stage], 2 * A_STAGE);
+                    tma_load_2d_pair(sA + stage * A_STAGE, &tmap, kb * F::BK, y,
+                                     full0 + stage * (uint32_t)sizeof(unsigned long long));
+                    ++issued;
+                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
+                }
+            }
+            // drain (rank 0): the last stages' loads of both CTAs must have landed before
+            // the pair may exit; rank 1 leaves only after the closing cluster barrier
+            if (rank == 0) {
+                const long long first = issued > nst ? issued - nst : 0;
+                for (long long i = first; i < issued; ++i)
+                    wait_bar<true>(&ctl->full_a[i % nst], (uint32_t)((i / nst) & 1), wctl, prm,
+                                   false);
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------ MMA issuer (rank 0 only)
+        if (rank == 0 && lane == 0) {
+            const uint32_t idesc = (1u << 4) | F::AB | ((uint32_t)(BN >> 3) << 17) |
+                                   ((uint32_t)(2 * BM >> 4) << 24);
+            uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
+            unsigned long long* last_bar = nullptr;
+            uint32_t last_par = 0;
+            bool ok = true;
+            for (long long t = pair; t < prm.num_tiles && ok; t += npairs) {
+                if (!wait_bar<true>(&ctl->tempty[acc], acc_phase ^ 1u, wctl, prm, true)) break;
+                fence_after();
+                const uint32_t d = tmem + acc * ACC_COLS;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!wait_bar<true>(&ctl->full_a[stage], phase, wctl, prm, true)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t a0 = su32(sA + stage * A_STAGE);
+                    const uint32_t b0 =
+                        su32(sB) + 128u * F::TS * (uint32_t)(kb * (F::BK / F::EPR));
+#pragma unroll
+                    for (int ks = 0; ks < KSTEPS; ++ks) {
+                        const uint64_t ad = sdesc(a0 + 32u * ks, 16u, 1024u, 2u);
+                        const uint64_t bd = sdesc(b0 + KSTEP_B * ks, LBO, SBO, 0u);
+                        umma_pair<DT>(d, ad, bd, idesc, (kb | ks) != 0);
+                    }
+                    umma_commit_pair(&ctl->empty[stage]);
+                    last_bar = &ctl->empty[stage];
+                    last_par = phase;
+                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                umma_commit_pair(&ctl->tfull[acc]);
+                last_bar = &ctl->tfull[acc];
+                last_par = acc_phase;
+                acc ^= 1u;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            if (last_bar) wait_bar(last_bar, last_par, wctl, prm, false);
+        }
+    } else if (warp >= 4) {
+        // ------------------------------------------------------ epilogue (both CTAs)
+        const int q = warp & 3;
+        const int half = lane & 1, ant_l = lane >> 1;
+        float4* stg = sEpi + q * 256;
+        uint32_t acc = 0, acc_phase = 0;
+        for (long long t = pair; t < prm.num_tiles; t += npairs) {
+            const long long rb = 2 * (t / num_jt) + rank;
+            long long j0;
+            int col0, valid;
+            pnce::lag_tile(prm.lags, BN, t % num_jt, j0, col0, valid);
+            const int ldH = prm.lags.ldH;
+            int got = 1;
+            if (lane == 0) got = wait_bar(&ctl->tfull[acc], acc_phase, wctl, prm, true);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) break;
+            fence_after();
+            const long long ant_base = rb * (BM / 2) + q * 16;
+            const long long my_ant = ant_base + ant_l;
+            const float rs = (my_ant < prm.A) ? __ldg(row_scale + my_ant) : 0.f;
+            const int nch = BN / 32;
+            for (int c = 0; c < nch; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * ACC_COLS + 32 * c, v);
+                if (c == nch - 1) {
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (rank == 0) mbar_arrive(&ctl->tempty[acc]);
+                        else mbar_arrive_remote(&ctl->tempty[acc], 0);
+                    }
+                }
+                float re[16], im[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float lo = __uint_as_float(v[31 - i]);
+                    const float hi = __uint_as_float(v[15 - i]);
+                    const float send = half ? lo : hi;
+                    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+                    re[i] = (half ? recv : lo) * rs;
+                    im[i] = (half ? hi : recv) * rs;
+                }
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int lc = 8 * half + k;
+                    const int pc = lc ^ (((ant_l & 3) << 1) | half);
+                    stg[ant_l * 16 + pc] =
+                        make_float4(re[2 * k], im[2 * k], re[2 * k + 1], im[2 * k + 1]);
+                }
+                __syncwarp();
+                const int jlo = BN - 32 - 32 * c;
+#pragma unroll
+                for (int it = 0; it < 8; ++it) {
+                    const int row = 2 * it + (lane >> 4), lc = lane & 15;
+                    const int pc = lc ^ (((row & 3) << 1) | (lc >> 3));
+                    const float4 val = stg[row * 16 + pc];
+                    const long long ant = ant_base + row;
+                    const int j = jlo + 2 * lc;
+                    if (ant < prm.A && j < valid) {
+                        const long long off = ant * ldH + col0;
+                        float2* dst = H + off + j;
+                        if (j + 1 < valid && (off & 1) == 0) {
+                            *reinterpret_cast<float4*>(dst) = val;
+                        } else {
+                            dst[0] = make_float2(val.x, val.y);
+                            if (j + 1 < valid) dst[1] = make_float2(val.z, val.w);
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+            acc ^= 1u;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    cluster_sync_all();      // the peer no longer reads this CTA's shared memory or barriers
+    if (warp == 2) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------------------- host
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -621,6 +960,49 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
         prm.b_region = STAGES * b_stage_bytes<DT>();
         prm.res_rows = 0;
     }
+    // 2-SM variant (opt-in while it is being evaluated): CTA pairs, each CTA with half of a
+    // BN-lag tile's pilot list; pairs stay on one lag block, so their count is a multiple
+    // of num_jt
+    const char* pairs_env = getenv("PNCE_TC_PAIRS");
+    if (pairs_env && pairs_env[0] == '1' && !(force && force[0] == '1')) {
+        const long long num_prb = (2 * A + 2 * BM - 1) / (2 * BM);
+        const long long ptiles = num_prb * prm.num_jt;
+        long long pairs = h->num_sms / 2;
+        if (pairs >= prm.num_jt) pairs = pairs / prm.num_jt * prm.num_jt;
+        if (pairs > ptiles) pairs = ptiles;
+        const long long res_cm2 = (long long)(prm.BN / 16 - 1) * F::QS +
+                                  ((long long)prm.num_kb * (F::BK / F::EPR) - 1) * F::TS + 1;
+        const long long res_bytes2 = (res_cm2 * 128 + 1023) / 1024 * 1024;
+        if (pairs >= 1 && pairs % prm.num_jt == 0 && prm.BN % 32 == 0 &&
+            (avail - res_bytes2) / A_STAGE >= MIN_RES_STAGES) {
+            TcParams pp = prm;
+            pp.num_tiles = ptiles;
+            pp.stages = (int)std::min<long long>(STAGES, (avail - res_bytes2) / A_STAGE);
+            pp.b_region = (int)res_bytes2;
+            pp.res_rows = (int)(res_cm2 * 8);
+            const size_t smem2 = smem_fixed() + (size_t)pp.stages * A_STAGE + pp.b_region;
+            if (cudaFuncSetAttribute(tc_pair_kernel<DT>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem2) != cudaSuccess)
+                return PNCE_ECUDA;
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)(2 * pairs), 1, 1);
+            cfg.blockDim = dim3(THREADS, 1, 1);
+            cfg.dynamicSmemBytes = smem2;
+            cfg.stream = s;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const cudaError_t le =
+                cudaLaunchKernelEx(&cfg, tc_pair_kernel<DT>, map, pilot->ext_bits_dev, factors, H, pp);
+            return le == cudaSuccess ? PNCE_OK : PNCE_ECUDA;
+        }
+    }
+
     const size_t smem = smem_fixed() + (size_t)prm.stages * A_STAGE + prm.b_region;
     if ((long long)smem > h->max_smem_optin) return PNCE_EUNSUPPORTED;
     auto kern = res ? tc_corr_kernel<DT, true> : tc_corr_kernel<DT, false>;
