@@ -156,10 +156,10 @@ __device__ __forceinline__ bool mbar_test(unsigned long long* b, uint32_t parity
 
 // Bounded wait for the phase of parity `parity` of barrier b.  honor_abort: give up as
 // soon as another role has latched an abort.  Returns false when the wait was abandoned.
+// The first test is inlined (the common case on the issue path); the loop is not.
 template <bool CL = false>
-__device__ __noinline__ bool wait_bar(unsigned long long* b, uint32_t parity, Ctl* ctl,
-                                      const TcParams& prm, bool honor_abort) {
-    if (mbar_test<CL>(b, parity)) return true;
+__device__ __noinline__ bool wait_bar_slow(unsigned long long* b, uint32_t parity, Ctl* ctl,
+                                           const TcParams& prm, bool honor_abort) {
     const unsigned long long t0 = gtime();
     for (;;) {
         if (mbar_test<CL>(b, parity)) return true;
@@ -170,6 +170,11 @@ __device__ __noinline__ bool wait_bar(unsigned long long* b, uint32_t parity, Ct
             return false;
         }
     }
+}
+template <bool CL = false>
+__device__ __forceinline__ bool wait_bar(unsigned long long* b, uint32_t parity, Ctl* ctl,
+                                         const TcParams& prm, bool honor_abort) {
+    return mbar_test<CL>(b, parity) || wait_bar_slow<CL>(b, parity, ctl, prm, honor_abort);
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
@@ -414,6 +419,11 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
         if (lane == 0) {
             const uint32_t idesc = (1u << 4) | F::AB | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(BM >> 4) << 24);
+            // a descriptor's start field is the byte address / 16 in its low 14 bits, and
+            // every operand lies below 256 KB, so moving a descriptor by a byte offset is a
+            // 64-bit add of offset / 16 (keeps the issue loop short)
+            const uint64_t adesc0 = sdesc(su32(sA), 16u, 1024u, 2u);
+            const uint64_t bdesc0 = sdesc(su32(sB), LBO, SBO, 0u);
             uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
             unsigned long long* last_bar = nullptr;
             uint32_t last_par = 0;
@@ -429,17 +439,14 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                         break;
                     }
                     fence_after();
-                    const uint32_t a0 = su32(sA + stage * A_STAGE);
+                    const uint64_t ad = adesc0 + (uint64_t)((stage * (uint32_t)A_STAGE) >> 4);
                     // resident: K block kb starts BK/EPR core matrices (times TS) further on
-                    const uint32_t b0 =
-                        RES ? su32(sB) + 128u * F::TS * (uint32_t)(kb * (F::BK / F::EPR))
-                            : su32(sB + stage * BSTAGE);
+                    const uint64_t bd =
+                        bdesc0 + (uint64_t)(RES ? (8u * F::TS * (uint32_t)(kb * (F::BK / F::EPR)))
+                                                : ((stage * (uint32_t)BSTAGE) >> 4));
 #pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ++ks) {
-                        const uint64_t ad = sdesc(a0 + 32u * ks, 16u, 1024u, 2u);
-                        const uint64_t bd = sdesc(b0 + KSTEP_B * ks, LBO, SBO, 0u);
-                        umma<DT>(d, ad, bd, idesc, (kb | ks) != 0);
-                    }
+                    for (int ks = 0; ks < KSTEPS; ++ks)
+                        umma<DT>(d, ad + 2u * ks, bd + (KSTEP_B >> 4) * ks, idesc, (kb | ks) != 0);
                     umma_commit(&ctl->empty[stage]);
                     last_bar = &ctl->empty[stage];
                     last_par = phase;
@@ -743,6 +750,8 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
         if (rank == 0 && lane == 0) {
             const uint32_t idesc = (1u << 4) | F::AB | ((uint32_t)(BN >> 3) << 17) |
                                    ((uint32_t)(2 * BM >> 4) << 24);
+            const uint64_t adesc0 = sdesc(su32(sA), 16u, 1024u, 2u);
+            const uint64_t bdesc0 = sdesc(su32(sB), LBO, SBO, 0u);
             uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
             unsigned long long* last_bar = nullptr;
             uint32_t last_par = 0;
@@ -757,15 +766,13 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                         break;
                     }
                     fence_after();
-                    const uint32_t a0 = su32(sA + stage * A_STAGE);
-                    const uint32_t b0 =
-                        su32(sB) + 128u * F::TS * (uint32_t)(kb * (F::BK / F::EPR));
+                    const uint64_t ad = adesc0 + (uint64_t)((stage * (uint32_t)A_STAGE) >> 4);
+                    const uint64_t bd =
+                        bdesc0 + (uint64_t)(8u * F::TS * (uint32_t)(kb * (F::BK / F::EPR)));
 #pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ++ks) {
-                        const uint64_t ad = sdesc(a0 + 32u * ks, 16u, 1024u, 2u);
-                        const uint64_t bd = sdesc(b0 + KSTEP_B * ks, LBO, SBO, 0u);
-                        umma_pair<DT>(d, ad, bd, idesc, (kb | ks) != 0);
-                    }
+                    for (int ks = 0; ks < KSTEPS; ++ks)
+                        umma_pair<DT>(d, ad + 2u * ks, bd + (KSTEP_B >> 4) * ks, idesc,
+                                      (kb | ks) != 0);
                     umma_commit_pair(&ctl->empty[stage]);
                     last_bar = &ctl->empty[stage];
                     last_par = phase;
