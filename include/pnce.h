@@ -90,8 +90,9 @@ pnce_status pnce_pilot_destroy(pnce_pilot* p);
 
 /*
  * Workspace bytes pnce_estimate needs for this shape and dtype (0 for FP32_SIMT).  The
- * tensor-core dtypes keep the quantised operand there: 2*F*M rows (re, im per antenna)
- * of ceil(N/64)*64 elements, plus per-antenna scales.  Returns 0 for invalid shapes.
+ * tensor-core dtypes keep the quantised operand there: 16*ceil(F*M/8) rows of
+ * ceil(N/64)*64 elements (row order as in pnce_quantize), plus per-antenna scales.
+ * Returns 0 for invalid shapes.
  */
 size_t pnce_workspace_size(int F, int M, int N, int K, int L, int dtype);
 
@@ -142,10 +143,14 @@ pnce_status pnce_estimate_ex(pnce_handle* h, const pnce_pilot* pilot, const void
  * tensor-core input format).  For antenna a = f*M + m: A_a = max_n max(|Re y|, |Im y|)
  * (exact in FP32), E_a = sum_n |y|^2 (FP64); scale 2^s_a with s_a = t - e where
  * A_a = mant * 2^e, mant in [0.5, 1), t = 15 (fp16) or 8 (e4m3), s_a = 0 for bf16,
- * tf32 and A_a = 0; s_a clamped to [-100, 100].  Writes, into workspace_dev, rows
- * 2a (real part) and 2a+1 (imaginary part) of round(y * 2^s_a) in dtype (round to
- * nearest even; e4m3 saturates at 448; tf32 rounds ties away), the per-antenna output
- * factor 2^-s_a / N (float32) and, if power_dev != NULL, E_a / N (float64 [F*M]).
+ * tf32 and A_a = 0; s_a clamped to [-100, 100].  Writes, into workspace_dev, the rows
+ * of round(y * 2^s_a) in dtype (round to nearest even; e4m3 saturates at 448; tf32
+ * rounds ties away): antennas in groups of 8, 16 rows per group, the real parts of the
+ * group's antennas first, so row 16*(a/8) + (a%8) holds the real part of antenna a and
+ * row 16*(a/8) + 8 + (a%8) its imaginary part; the rows of antennas >= F*M in the last
+ * group are zero.  Rows hold ceil(N/64)*64 elements (the tail past N is not written).
+ * Also writes the per-antenna output factor 2^-s_a / N (float32) after the rows and, if
+ * power_dev != NULL, E_a / N (float64 [F*M]).
  * exps_dev (int32 [F*M], may be NULL) receives s_a.  dtype must not be FP32_SIMT.
  */
 pnce_status pnce_quantize(pnce_handle* h, const void* Y_dev, int F, int M, int N, int dtype,

@@ -228,12 +228,21 @@ def estimate(Y: torch.Tensor, pilot: Pilot, K: int, L: int, dtype="fp32", out=No
     return H
 
 
+def operand_rows(A: int):
+    """Row indices (real, imaginary) of antennas 0..A-1 in the quantised operand."""
+    a = torch.arange(A, dtype=torch.int64)
+    re = 16 * (a // 8) + a % 8
+    return re, re + 8
+
+
 def quantize(Y: torch.Tensor, dtype, workspace=None, want_power=False):
     """Run only the quantisation step; returns a dict of views into the workspace.
 
-    'q': the operand as raw integer codes [F*M*2, pitch] (uint16 for fp16/bf16, int32 for
-    tf32, uint8 for e4m3), 'factor': float32 [F*M] = 2^-s / N, 'exps': int32 s,
-    'power': float64 mean power (if want_power), 'workspace': the buffer.
+    'q': the operand as raw integer codes [16*ceil(F*M/8), pitch] (uint16 for fp16/bf16,
+    int32 for tf32, uint8 for e4m3) in groups of 8 antennas: row 16*(a//8) + a%8 holds the
+    real part of antenna a = f*M + m, row 16*(a//8) + 8 + a%8 its imaginary part
+    (operand_rows() gives the row indices); 'factor': float32 [F*M] = 2^-s / N, 'exps':
+    int32 s, 'power': float64 mean power (if want_power), 'workspace': the buffer.
     """
     F, M, N = _check_y(Y)
     dt = _dt(dtype)
@@ -250,7 +259,7 @@ def quantize(Y: torch.Tensor, dtype, workspace=None, want_power=False):
               "pnce_quantize")
     pitch = (N + 63) // 64 * 64
     eb = {1: 4, 2: 2, 3: 2, 4: 1}[dt]
-    rows = 2 * F * M
+    rows = 16 * ((F * M + 7) // 8)
     abytes = rows * pitch * eb
     view_dt = {4: torch.int32, 2: torch.int16, 1: torch.uint8}[eb]
     q = ws[:abytes].view(view_dt).view(rows, pitch)

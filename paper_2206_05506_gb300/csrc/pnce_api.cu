@@ -40,16 +40,18 @@ pnce_status from_cuda(cudaError_t e) { return e == cudaSuccess ? PNCE_OK : PNCE_
 // Frame chunks for pnce_estimate.  Off by default: the quantiser of a batch runs, then the
 // tensor-core correlation.  PNCE_OVERLAP_CHUNKS=n (2..8) splits a large batch into n frame
 // chunks and quantises chunk i+1 on one handle stream while chunk i is correlated on
-// another.  Measured on GB300 (512 x 128 x 4095, fp16): 1.716 ms per estimate sequential,
-// 1.743 / 1.653 / 1.650 / 1.798 / 1.691 ms with 2 / 3 / 4 / 6 / 8 chunks -- the quantiser
-// and the correlation compete for the SMs' L1/shared-memory data path, so overlapping buys
-// at most 4 %, and only when each chunk keeps >= 8 waves of 128 x 256 tiles.
+// another.  Measured on GB300 (512 x 128 x 4095, fp16, with an earlier correlation
+// kernel): 1.716 ms per estimate sequential, 1.743 / 1.653 / 1.650 / 1.798 / 1.691 ms with
+// 2 / 3 / 4 / 6 / 8 chunks -- the quantiser and the correlation compete for the SMs'
+// L1/shared-memory data path, so overlapping buys at most 4 %, and only when each chunk
+// keeps >= 8 waves of 128 x 256 tiles.  Chunks must hold whole 8-antenna operand groups.
 int estimate_chunks(const pnce_handle* h, int F, int M, int N, int KL) {
     (void)N;
     const char* e = getenv("PNCE_OVERLAP_CHUNKS");
     long long n = e ? atoll(e) : 1;
     if (n <= 1) return 1;
     if (n > 8) n = 8;
+    if ((((long long)F + n - 1) / n * M) % 8 != 0) return 1;
     const long long row_blocks_per_frame = (2LL * M + 127) / 128;
     const long long jt = (KL + 255) / 256;
     const long long tiles = (long long)F * row_blocks_per_frame * jt;
@@ -78,8 +80,8 @@ pnce_status estimate_overlapped(pnce_handle* h, const pnce_pilot* pilot, const f
     for (int f0 = 0; f0 < F; f0 += per, ++i) {
         const int fc = (F - f0 < per) ? (F - f0) : per;
         const long long a0 = (long long)f0 * M, ac = (long long)fc * M;
-        // chunk i owns operand rows [2 a0, 2 (a0 + ac)) and factors [a0, a0 + ac) of the
-        // whole-batch layout, so chunks never share memory
+        // chunk i owns operand rows [2 a0, 2 a0 + operand_rows(ac)) and factors [a0, a0 + ac)
+        // of the whole-batch layout (a0 is a multiple of 8), so chunks never share memory
         void* op = operand + (size_t)(2 * a0) * row_bytes;
         float* fa = factors + a0;
         cudaError_t e;

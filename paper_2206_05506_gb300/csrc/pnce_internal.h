@@ -108,8 +108,16 @@ inline int row_pitch(int N) { return (int)round_up((size_t)N, kRowPad); }
 int elem_bytes(int dtype);              // bytes per quantised element (0 for FP32_SIMT)
 
 // Workspace carve-up for the tensor-core path.
+// Operand row order: antennas in groups of 8, 16 rows per group -- the real parts of the
+// group's 8 antennas, then their imaginary parts (so a 16-lane TMEM block of the product
+// holds both parts of 8 antennas).  Rows of antennas >= A in the last group are zero.
+__host__ __device__ inline long long operand_rows(long long A) { return 16 * ((A + 7) / 8); }
+__host__ __device__ inline long long operand_row(long long a, int part) {
+    return 16 * (a >> 3) + 8 * part + (a & 7);
+}
+
 struct QuantLayout {
-    size_t a_offset, a_bytes;           // [2*A][pitch] quantised operand
+    size_t a_offset, a_bytes;           // [operand_rows(A)][pitch] quantised operand
     size_t scale_offset;                // float[A]: 2^-s_a / N
     size_t total;
 };
@@ -124,7 +132,8 @@ cudaError_t launch_simt_bits_ex(const pnce_pilot* pilot, const float2* Y, long l
                                 cudaStream_t s);
 cudaError_t launch_simt_real(const float* p, bool tanh_map, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s);
-// operand: [2A][row_pitch(N)] elements; factors: float[A] (2^-s_a / N).  max_blocks > 0
+// operand: [operand_rows(A)][row_pitch(N)] elements in operand_row order; factors:
+// float[A] (2^-s_a / N).  max_blocks > 0
 // caps the grid (blocks then loop over antennas), to leave room for a concurrent kernel.
 cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* operand,
                             float* factors, int32_t* exps, double* power, cudaStream_t s,

@@ -5,8 +5,9 @@
 // when the caller asks for it, E_a = sum |y|^2 in FP64 (squares of FP32 values are exact
 // in FP64; GB300's FP64 rate is low, so the estimate path does not request it); the
 // power-of-two scale 2^s_a is taken from A_a; pass 2 re-reads the row (an L2 hit) and
-// writes rows 2a (real) and 2a+1 (imaginary) of round(y 2^s_a), four samples per thread
-// per step.
+// writes rows operand_row(a, 0) (real) and operand_row(a, 1) (imaginary) of
+// round(y 2^s_a), four samples per thread per step.  Blocks past the last antenna zero
+// the padding rows of the last 8-antenna group.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -91,7 +92,17 @@ quantize_kernel(const float2* __restrict__ Y, long long A, int N, long long y_st
     __shared__ float s_scale;
     const int tid = threadIdx.x;
 
-  for (long long a = blockIdx.x; a < A; a += gridDim.x) {
+  const long long A_pad = (A + 7) / 8 * 8;
+  for (long long a = blockIdx.x; a < A_pad; a += gridDim.x) {
+    if (a >= A) {                  // padding antenna of the last group: zero rows
+        const float z[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int n = 4 * tid; n < N; n += 4 * THREADS) {
+            const int valid = min(4, N - n);
+            store4<DT>(Q, pnce::operand_row(a, 0), pitch, n, z, valid);
+            store4<DT>(Q, pnce::operand_row(a, 1), pitch, n, z, valid);
+        }
+        continue;
+    }
     const float2* row = Y + a * y_stride;
 
     float amax = 0.f;
@@ -145,8 +156,8 @@ quantize_kernel(const float2* __restrict__ Y, long long A, int N, long long y_st
                 im[i] = y.y * sc;
             }
         }
-        store4<DT>(Q, 2 * a, pitch, n, re, valid);
-        store4<DT>(Q, 2 * a + 1, pitch, n, im, valid);
+        store4<DT>(Q, pnce::operand_row(a, 0), pitch, n, re, valid);
+        store4<DT>(Q, pnce::operand_row(a, 1), pitch, n, im, valid);
     }
     __syncthreads();   // s_max / s_scale are reused by the next antenna
   }
@@ -157,7 +168,7 @@ cudaError_t launch_dt(const float2* Y, long long A, int N, void* operand, float*
                       int32_t* exps, double* power, cudaStream_t s, int max_blocks,
                       long long y_stride) {
     const float invN = (float)(1.0 / (double)N);
-    long long grid = A;
+    long long grid = (A + 7) / 8 * 8;               // padding antennas included
     if (max_blocks > 0 && grid > max_blocks) grid = max_blocks;
     if (grid > 0x7fffffffLL) grid = 0x7fffffffLL;
     auto kern = power ? quantize_kernel<DT, true> : quantize_kernel<DT, false>;
@@ -183,7 +194,7 @@ int elem_bytes(int dtype) {
 QuantLayout quant_layout(long long A, int N, int dtype) {
     QuantLayout l{};
     l.a_offset = 0;
-    l.a_bytes = (size_t)(2 * A) * (size_t)row_pitch(N) * (size_t)elem_bytes(dtype);
+    l.a_bytes = (size_t)operand_rows(A) * (size_t)row_pitch(N) * (size_t)elem_bytes(dtype);
     l.scale_offset = round_up(l.a_bytes, 256);
     l.total = round_up(l.scale_offset + (size_t)A * sizeof(float), 256);
     return l;

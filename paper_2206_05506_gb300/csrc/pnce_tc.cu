@@ -3,8 +3,9 @@
 //
 //   C[r][j] = sum_n A[r][n] * B[n][j],  B[n][j] = p[(n - j) mod N]  (the circulant, Eq. 2)
 //
-// A: the quantised received block, rows r = 2a (real) / 2a+1 (imaginary) of antenna a,
-//    staged 128 rows x 128 B per pipeline stage by TMA with the 128-byte swizzle.
+// A: the quantised received block in 8-antenna groups of 16 rows (the 8 real parts, then
+//    the 8 imaginary parts), staged 128 rows x 128 B per pipeline stage by TMA with the
+//    128-byte swizzle.
 // B: never stored in HBM.  The lag order inside a tile is reversed (tile column i holds
 //    lag j0 + BN - 1 - i, j0 the tile's first lag: k*L-contiguous tiles, or per-transmitter
 //    tiles when the transmitters' cyclic shifts are spread out), which turns the Toeplitz tile into a Hankel one: the value at
@@ -17,11 +18,12 @@
 //    block of the CTA's lag block (N/8 + BN/8 core matrices for 16-bit types, ~70 KB at
 //    N = 4095) is generated once at kernel start and stays resident ("resident pilot");
 //    otherwise one warp regenerates each stage's list (<= 70 core matrices, <= 9 KB).
-// Epilogue: tcgen05.ld of 32 accumulator columns, re/im pairing by lane shuffles (rows 2a,
-//    2a+1 are adjacent TMEM lanes), the per-antenna factor 2^-s_a / N, lag order restored,
-//    staged through a bank-conflict-free swizzled buffer and written as whole 256-byte
-//    rows of H.  TMEM holds two 256-column accumulators so the epilogue of one tile
-//    overlaps the products of the next.
+// Epilogue: tcgen05.ld in the 16x256b shape hands each thread the real and imaginary
+//    accumulators of one antenna for two adjacent columns (the group layout puts the two
+//    parts 8 TMEM lanes apart), so after the per-antenna factor 2^-s_a / N each thread
+//    writes one complex lag pair (16 B; an antenna's 4 threads write 64 contiguous bytes)
+//    with no shuffles and no shared-memory staging.  TMEM holds two 256-column
+//    accumulators so the epilogue of one tile overlaps the products of the next.
 //
 // Warp roles (256 threads, persistent, one CTA per SM): warp 0 TMA producer, warp 1 pilot
 // tile generator, warp 2 TMEM allocator + MMA issuer, warps 4-7 epilogue (TMEM lane
@@ -50,7 +52,6 @@ constexpr int A_STAGE = BM * 128;         // 16 KB
 constexpr int ACC_COLS = 256;
 constexpr int TMEM_COLS = 512;
 constexpr int MAX_BN = 256;
-constexpr int EPI_BYTES = 4 * 4096;       // 4 warps x (16 antennas x 32 lags x 8 B)
 
 struct TcParams {
     int N;
@@ -107,7 +108,7 @@ struct Ctl {
     int abort_flag;
 };
 
-constexpr size_t smem_fixed() { return 1024 /* alignment slack */ + EPI_BYTES + sizeof(Ctl); }
+constexpr size_t smem_fixed() { return 1024 /* alignment slack */ + sizeof(Ctl); }
 
 // ------------------------------------------------------------------ PTX helpers
 
@@ -176,6 +177,24 @@ __device__ __forceinline__ bool wait_bar(unsigned long long* b, uint32_t parity,
                                          const TcParams& prm, bool honor_abort) {
     return mbar_test<CL>(b, parity) || wait_bar_slow<CL>(b, parity, ctl, prm, honor_abort);
 }
+// The same bounded wait for a role that is not on the issue path (the epilogue waiting
+// for an accumulator, ~a tile's worth of MMAs): polls with a short sleep in between, so
+// that the polling does not take issue slots and shared-memory cycles from the producer
+// and the MMA issuer.
+__device__ __noinline__ bool wait_bar_sleepy(unsigned long long* b, uint32_t parity, Ctl* ctl,
+                                             const TcParams& prm) {
+    const unsigned long long t0 = gtime();
+    for (;;) {
+        if (mbar_test(b, parity)) return true;
+        if (*(volatile int*)&ctl->abort_flag) return false;
+        if (gtime() - t0 > prm.wait_limit_ns) {
+            *(volatile int*)&ctl->abort_flag = 1;
+            atomicCAS(prm.err, 0, (int)PNCE_ETIMEOUT);
+            return false;
+        }
+        __nanosleep(256);
+    }
+}
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
                                             unsigned long long* bar) {
@@ -237,9 +256,12 @@ __device__ __forceinline__ void umma_commit(unsigned long long* bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+// 16 TMEM lanes x 64 columns: thread t receives, for each block x < 8 of 8 columns,
+// v[4x] v[4x+1] = lane t/4, columns 8x + 2(t%4) + {0,1}, and v[4x+2] v[4x+3] = lane 8 + t/4,
+// the same columns
+__device__ __forceinline__ void tmem_ld16x256b_x8(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "tcgen05.ld.sync.aligned.16x256b.x8.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
         "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
         "[%32];"
@@ -250,7 +272,62 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
           "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
           "=r"(v[31])
         : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Epilogue of one 128-row accumulator (TMEM columns [0, BN) at `tacc`) by epilogue warp q,
+// which owns TMEM lanes 32q .. 32q+31: operand rows of the 8-antenna groups 2q and 2q+1
+// of the row block (first antenna ant_base).  Column c of the tile holds tile-local lag
+// BN-1-c.  Thread t keeps antenna t/4 of each group: from the 16x256b layout it holds the
+// real (lane t/4) and imaginary (lane 8+t/4) parts of columns 2u, 2u+1, i.e. the complex
+// estimates of two adjacent lags, scaled and stored as one 16-byte write (4 threads of an
+// antenna write 64 contiguous bytes).  `release` runs once the last TMEM load is done, so
+// the MMA issuer may reuse the accumulator while the stores drain.
+template <typename Release>
+__device__ __forceinline__ void drain_accumulator(uint32_t tacc, int q, int lane,
+                                                  long long ant_base, const float* row_scale,
+                                                  float2* __restrict__ H, long long A, int ldH,
+                                                  int BN, int col0, int valid, Release release) {
+    const int g = lane >> 2, u4 = lane & 3;
+    long long ant[2];
+    float rs[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        ant[h] = ant_base + 16 * q + 8 * h + g;
+        rs[h] = ant[h] < A ? __ldg(row_scale + ant[h]) : 0.f;
+    }
+    const int nch = BN / 64 + ((BN & 63) ? 1 : 0);     // chunks of 64 columns (BN % 32 == 0)
+    for (int c = 0; c < nch; ++c) {
+        uint32_t v[2][32];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            tmem_ld16x256b_x8(tacc + ((uint32_t)(32 * q + 16 * h) << 16) + 64u * c, v[h]);
+        tmem_wait_ld();
+        if (c == nch - 1) release();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (ant[h] >= A) continue;
+            const long long off = ant[h] * ldH + col0;
+            float2* row = H + off;
+#pragma unroll
+            for (int x = 0; x < 8; ++x) {
+                const int col = 64 * c + 8 * x + 2 * u4;        // even column of the pair
+                const int j = BN - 2 - col;                     // lag of column col + 1
+                if (j < 0 || j >= valid) continue;
+                const float4 val = make_float4(
+                    __uint_as_float(v[h][4 * x + 1]) * rs[h], __uint_as_float(v[h][4 * x + 3]) * rs[h],
+                    __uint_as_float(v[h][4 * x]) * rs[h], __uint_as_float(v[h][4 * x + 2]) * rs[h]);
+                if (j + 1 < valid && (off & 1) == 0) {
+                    *reinterpret_cast<float4*>(row + j) = val;
+                } else {
+                    row[j] = make_float2(val.x, val.y);
+                    if (j + 1 < valid) row[j + 1] = make_float2(val.z, val.w);
+                }
+            }
+        }
+    }
 }
 
 // --------------------------------------------------------- pilot operand tiles
@@ -322,8 +399,7 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     const int nst = prm.stages;
     unsigned char* sA = base;
     unsigned char* sB = sA + nst * A_STAGE;
-    float4* sEpi = reinterpret_cast<float4*>(sB + prm.b_region);
-    Ctl* ctl = reinterpret_cast<Ctl*>(reinterpret_cast<unsigned char*>(sEpi) + EPI_BYTES);
+    Ctl* ctl = reinterpret_cast<Ctl*>(sB + prm.b_region);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int BN = prm.BN, num_jt = prm.num_jt, num_kb = prm.num_kb;
@@ -464,75 +540,24 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     } else if (warp >= 4) {
         // --------------------------------------------------------------- epilogue
         const int q = warp & 3;                 // TMEM lane quarter
-        const int half = lane & 1, ant_l = lane >> 1;
-        float4* stg = sEpi + q * 256;
         uint32_t acc = 0, acc_phase = 0;
         for (long long t = blockIdx.x; t < prm.num_tiles; t += gridDim.x) {
             const long long rb = t / num_jt;
             long long j0;                       // first lag of the tile (unused here)
             int col0, valid;                    // first output column, lags kept
             pnce::lag_tile(prm.lags, BN, t % num_jt, j0, col0, valid);
-            const int ldH = prm.lags.ldH;
             int got = 1;
-            if (lane == 0) got = wait_bar(&ctl->tfull[acc], acc_phase, ctl, prm, true);
+            if (lane == 0) got = wait_bar_sleepy(&ctl->tfull[acc], acc_phase, ctl, prm);
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) break;
             fence_after();
-            const long long ant_base = rb * (BM / 2) + q * 16;
-            const long long my_ant = ant_base + ant_l;
-            const float rs = (my_ant < prm.A) ? __ldg(row_scale + my_ant) : 0.f;
-            const int nch = BN / 32;
-            for (int c = 0; c < nch; ++c) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * ACC_COLS + 32 * c, v);
-                if (c == nch - 1) {
-                    fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
-                }
-                // column 32c + i holds lag jlo + 31 - i; this lane keeps 16 lags of its
-                // antenna: lags jlo + 16*half + i, i < 16
-                float re[16], im[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float lo = __uint_as_float(v[31 - i]);      // lag jlo + i
-                    const float hi = __uint_as_float(v[15 - i]);      // lag jlo + 16 + i
-                    const float send = half ? lo : hi;
-                    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
-                    re[i] = (half ? recv : lo) * rs;
-                    im[i] = (half ? hi : recv) * rs;
-                }
-                // staging: row ant_l (256 B = 16 chunks of 2 complex), chunk 8*half + k
-                // stored at (8*half + k) ^ ((ant_l & 3) << 1 | half)
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int lc = 8 * half + k;
-                    const int pc = lc ^ (((ant_l & 3) << 1) | half);
-                    stg[ant_l * 16 + pc] =
-                        make_float4(re[2 * k], im[2 * k], re[2 * k + 1], im[2 * k + 1]);
-                }
-                __syncwarp();
-                const int jlo = BN - 32 - 32 * c;       // tile-local lag of chunk column 31
-#pragma unroll
-                for (int it = 0; it < 8; ++it) {
-                    const int row = 2 * it + (lane >> 4), lc = lane & 15;
-                    const int pc = lc ^ (((row & 3) << 1) | (lc >> 3));
-                    const float4 val = stg[row * 16 + pc];
-                    const long long ant = ant_base + row;
-                    const int j = jlo + 2 * lc;
-                    if (ant < prm.A && j < valid) {
-                        const long long off = ant * ldH + col0;
-                        float2* dst = H + off + j;
-                        if (j + 1 < valid && (off & 1) == 0) {
-                            *reinterpret_cast<float4*>(dst) = val;
-                        } else {
-                            dst[0] = make_float2(val.x, val.y);
-                            if (j + 1 < valid) dst[1] = make_float2(val.z, val.w);
-                        }
-                    }
-                }
-                __syncwarp();
-            }
+            unsigned long long* te = &ctl->tempty[acc];
+            drain_accumulator(tmem + acc * ACC_COLS, q, lane, rb * (BM / 2), row_scale, H,
+                              prm.A, prm.lags.ldH, BN, col0, valid, [&] {
+                                  fence_before();
+                                  __syncwarp();
+                                  if (lane == 0) mbar_arrive(te);
+                              });
             acc ^= 1u;
             if (acc == 0) acc_phase ^= 1u;
         }
@@ -555,8 +580,8 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
 // the BN lags (rank 0: tile columns [0, BN/2), rank 1: [BN/2, BN)), so each SM reads half
 // the pilot operand per MMA.  Rank 0 issues the MMAs for both; the operand loads of both
 // CTAs complete on rank 0's stage barrier, its commits arrive on the barriers of both CTAs
-// (multicast), and each CTA drains its own 128 accumulator rows, the odd CTA releasing
-// rank 0's accumulator barrier remotely.
+// (one commit per CTA), and each CTA drains its own 128 accumulator rows, the odd CTA
+// releasing rank 0's accumulator barrier remotely.
 
 struct PairCtl {
     unsigned long long full_a[STAGES];
@@ -597,14 +622,20 @@ __device__ __forceinline__ void mbar_arrive_remote(unsigned long long* local, ui
     asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote)
                  : "memory");
 }
-// commit the issuing thread's MMAs to the barrier at this offset in both CTAs of the pair
+__device__ __forceinline__ uint32_t cluster_addr(const void* local, uint32_t rank) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(su32(local)), "r"(rank));
+    return remote;
+}
+// commit the issuing thread's MMAs to the barrier at this offset in each CTA of the pair
+// (one commit per CTA; each tracks all MMAs the thread issued before it)
 __device__ __forceinline__ void umma_commit_pair(unsigned long long* bar) {
-    const uint16_t mask = 3;
-    asm volatile(
-        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(su32(bar)),
-        "h"(mask)
-        : "memory");
+#pragma unroll
+    for (uint32_t r = 0; r < 2; ++r)
+        asm volatile(
+            "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                cluster_addr(bar, r))
+            : "memory");
 }
 
 // TMA load into this CTA's shared memory whose completion is counted on the barrier at
@@ -617,12 +648,6 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* m
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar_cluster)
         : "memory");
 }
-__device__ __forceinline__ uint32_t cluster_addr(const void* local, uint32_t rank) {
-    uint32_t remote;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(su32(local)), "r"(rank));
-    return remote;
-}
-
 template <int DT>
 __device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                           uint32_t accumulate) {
@@ -662,8 +687,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     const int nst = prm.stages;
     unsigned char* sA = base;
     unsigned char* sB = sA + nst * A_STAGE;
-    float4* sEpi = reinterpret_cast<float4*>(sB + prm.b_region);
-    PairCtl* ctl = reinterpret_cast<PairCtl*>(reinterpret_cast<unsigned char*>(sEpi) + EPI_BYTES);
+    PairCtl* ctl = reinterpret_cast<PairCtl*>(sB + prm.b_region);
     Ctl* wctl = reinterpret_cast<Ctl*>(ctl);    // abort flag shared with wait_bar
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -790,74 +814,27 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     } else if (warp >= 4) {
         // ------------------------------------------------------ epilogue (both CTAs)
         const int q = warp & 3;
-        const int half = lane & 1, ant_l = lane >> 1;
-        float4* stg = sEpi + q * 256;
         uint32_t acc = 0, acc_phase = 0;
         for (long long t = pair; t < prm.num_tiles; t += npairs) {
             const long long rb = 2 * (t / num_jt) + rank;
             long long j0;
             int col0, valid;
             pnce::lag_tile(prm.lags, BN, t % num_jt, j0, col0, valid);
-            const int ldH = prm.lags.ldH;
             int got = 1;
-            if (lane == 0) got = wait_bar(&ctl->tfull[acc], acc_phase, wctl, prm, true);
+            if (lane == 0) got = wait_bar_sleepy(&ctl->tfull[acc], acc_phase, wctl, prm);
             got = __shfl_sync(0xffffffffu, got, 0);
             if (!got) break;
             fence_after();
-            const long long ant_base = rb * (BM / 2) + q * 16;
-            const long long my_ant = ant_base + ant_l;
-            const float rs = (my_ant < prm.A) ? __ldg(row_scale + my_ant) : 0.f;
-            const int nch = BN / 32;
-            for (int c = 0; c < nch; ++c) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + acc * ACC_COLS + 32 * c, v);
-                if (c == nch - 1) {
-                    fence_before();
-                    __syncwarp();
-                    if (lane == 0) {
-                        if (rank == 0) mbar_arrive(&ctl->tempty[acc]);
-                        else mbar_arrive_remote(&ctl->tempty[acc], 0);
-                    }
-                }
-                float re[16], im[16];
-#pragma unroll
-                for (int i = 0; i < 16; ++i) {
-                    const float lo = __uint_as_float(v[31 - i]);
-                    const float hi = __uint_as_float(v[15 - i]);
-                    const float send = half ? lo : hi;
-                    const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
-                    re[i] = (half ? recv : lo) * rs;
-                    im[i] = (half ? hi : recv) * rs;
-                }
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int lc = 8 * half + k;
-                    const int pc = lc ^ (((ant_l & 3) << 1) | half);
-                    stg[ant_l * 16 + pc] =
-                        make_float4(re[2 * k], im[2 * k], re[2 * k + 1], im[2 * k + 1]);
-                }
-                __syncwarp();
-                const int jlo = BN - 32 - 32 * c;
-#pragma unroll
-                for (int it = 0; it < 8; ++it) {
-                    const int row = 2 * it + (lane >> 4), lc = lane & 15;
-                    const int pc = lc ^ (((row & 3) << 1) | (lc >> 3));
-                    const float4 val = stg[row * 16 + pc];
-                    const long long ant = ant_base + row;
-                    const int j = jlo + 2 * lc;
-                    if (ant < prm.A && j < valid) {
-                        const long long off = ant * ldH + col0;
-                        float2* dst = H + off + j;
-                        if (j + 1 < valid && (off & 1) == 0) {
-                            *reinterpret_cast<float4*>(dst) = val;
-                        } else {
-                            dst[0] = make_float2(val.x, val.y);
-                            if (j + 1 < valid) dst[1] = make_float2(val.z, val.w);
-                        }
-                    }
-                }
-                __syncwarp();
-            }
+            unsigned long long* te = &ctl->tempty[acc];
+            drain_accumulator(tmem + acc * ACC_COLS, q, lane, rb * (BM / 2), row_scale, H,
+                              prm.A, prm.lags.ldH, BN, col0, valid, [&] {
+                                  fence_before();
+                                  __syncwarp();
+                                  if (lane == 0) {
+                                      if (rank == 0) mbar_arrive(te);
+                                      else mbar_arrive_remote(te, 0);
+                                  }
+                              });
             acc ^= 1u;
             if (acc == 0) acc_phase ^= 1u;
         }
@@ -911,7 +888,7 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     if (DT == PNCE_BF16) ty = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     if (DT == PNCE_FP8E4M3) ty = CU_TENSOR_MAP_DATA_TYPE_UINT8;
     if (DT == PNCE_TF32) ty = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)(2 * A)};
+    const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)pnce::operand_rows(A)};
     const cuuint64_t strides[1] = {(cuuint64_t)pnce::row_pitch(N) * pnce::elem_bytes(DT)};
     const cuuint32_t box[2] = {(cuuint32_t)F::BK, (cuuint32_t)BM};
     const cuuint32_t estr[2] = {1, 1};
@@ -933,7 +910,7 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     const long long njt = pnce::lag_tiles(lags, prm.BN);
     if (njt > (1 << 30)) return PNCE_EUNSUPPORTED;
     prm.num_jt = (int)njt;
-    const long long num_rb = (2 * A + BM - 1) / BM;
+    const long long num_rb = (pnce::operand_rows(A) + BM - 1) / BM;
     prm.num_tiles = num_rb * prm.num_jt;
     prm.num_kb = (N + F::BK - 1) / F::BK;
     prm.wait_limit_ns = wait_limit_ns();
@@ -972,7 +949,7 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     // of num_jt
     const char* pairs_env = getenv("PNCE_TC_PAIRS");
     if (pairs_env && pairs_env[0] == '1' && !(force && force[0] == '1')) {
-        const long long num_prb = (2 * A + 2 * BM - 1) / (2 * BM);
+        const long long num_prb = (pnce::operand_rows(A) + 2 * BM - 1) / (2 * BM);
         const long long ptiles = num_prb * prm.num_jt;
         long long pairs = h->num_sms / 2;
         if (pairs >= prm.num_jt) pairs = pairs / prm.num_jt * prm.num_jt;

@@ -108,9 +108,18 @@ def test_quantizer_bit_exact(pk, shape, dtype):
     res = pk.quantize(torch.from_numpy(Y).to(dev), dtype, want_power=True)
     Q, se = O.quantize(Y, dtype)
     N = Y.shape[2]
-    got = _decode(res["q"], dtype)[:, :N].reshape(F * M, 2, N)
-    want = np.stack([Q.real, Q.imag], axis=-2).reshape(F * M, 2, N)
+    A = F * M
+    rows = _decode(res["q"], dtype)[:, :N]
+    assert rows.shape[0] == 16 * ((A + 7) // 8)
+    # groups of 8 antennas: real rows, then imaginary rows; padding rows zero
+    a = np.arange(A)
+    re_rows = 16 * (a // 8) + a % 8
+    got = np.stack([rows[re_rows], rows[re_rows + 8]], axis=1)
+    want = np.stack([Q.real, Q.imag], axis=-2).reshape(A, 2, N)
     assert np.array_equal(got, want)
+    pad = np.setdiff1d(np.arange(rows.shape[0]), np.concatenate([re_rows, re_rows + 8]))
+    assert np.all(rows[pad] == 0)
+    assert np.array_equal(pk.operand_rows(A)[0].numpy(), re_rows)
     assert np.array_equal(res["exps"].cpu().numpy(), se.reshape(-1))
     fac = np.float32(1.0 / N) * np.ldexp(np.float32(1.0), -se.reshape(-1)).astype(np.float32)
     assert np.array_equal(res["factor"].cpu().numpy(), fac)

@@ -56,9 +56,10 @@ def test_workspace_size_rules(lib):
     assert lib.pnce_workspace_size(1, 8, 127, 8, 16, 2) == 0
     assert lib.pnce_workspace_size(0, 8, 127, 2, 16, 2) == 0
     assert lib.pnce_workspace_size(1, 8, 127, 2, 16, 99) == 0
-    # fp16: 2*F*M rows of ceil(N/64)*64 halfs, then F*M float factors, 256-byte rounded
+    # fp16: 16*ceil(F*M/8) rows (8-antenna groups) of ceil(N/64)*64 halfs, then F*M float
+    # factors, 256-byte rounded
     F, M, N = 3, 5, 1023
-    rows, pitch = 2 * F * M, 1024
+    rows, pitch = 16 * ((F * M + 7) // 8), 1024
     a = rows * pitch * 2
     want = ((a + 255) // 256 * 256 + 4 * F * M + 255) // 256 * 256
     assert lib.pnce_workspace_size(F, M, N, 8, 64, 2) == want
