@@ -52,6 +52,7 @@ constexpr int A_STAGE = BM * 128;         // 16 KB
 constexpr int ACC_COLS = 256;
 constexpr int TMEM_COLS = 512;
 constexpr int MAX_BN = 256;
+constexpr double EPI_SPREAD = 0.5;        // share of a tile's MMA time the epilogue spans
 
 struct TcParams {
     int N;
@@ -67,6 +68,7 @@ struct TcParams {
     int drop_first_arrive;  // test hook: the per-stage pilot generator withholds its first
                             // arrive, so the MMA issuer's bounded wait must run out
     unsigned long long wait_limit_ns;
+    long long epi_spacing;  // SM cycles between the epilogue's 64-column chunks (0: none)
     int* err;
 };
 
@@ -284,12 +286,17 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // real (lane t/4) and imaginary (lane 8+t/4) parts of columns 2u, 2u+1, i.e. the complex
 // estimates of two adjacent lags, scaled and stored as one 16-byte write (4 threads of an
 // antenna write 64 contiguous bytes).  `release` runs once the last TMEM load is done, so
-// the MMA issuer may reuse the accumulator while the stores drain.
+// the MMA issuer may reuse the accumulator while the stores drain.  The chunks start
+// `spacing` SM cycles apart: a tile's stores (128 KB per CTA at BN = 256) issued in one
+// burst take the L1 data path from the tensor cores' operand reads for a while, spread
+// over the next tile's products they cost less (measured: ~4 % of the kernel in a burst).
 template <typename Release>
 __device__ __forceinline__ void drain_accumulator(uint32_t tacc, int q, int lane,
                                                   long long ant_base, const float* row_scale,
                                                   float2* __restrict__ H, long long A, int ldH,
-                                                  int BN, int col0, int valid, Release release) {
+                                                  int BN, int col0, int valid,
+                                                  long long spacing, Release release) {
+    const long long c0 = clock64();
     const int g = lane >> 2, u4 = lane & 3;
     long long ant[2];
     float rs[2];
@@ -300,6 +307,10 @@ __device__ __forceinline__ void drain_accumulator(uint32_t tacc, int q, int lane
     }
     const int nch = BN / 64 + ((BN & 63) ? 1 : 0);     // chunks of 64 columns (BN % 32 == 0)
     for (int c = 0; c < nch; ++c) {
+        if (c > 0 && spacing > 0) {
+            // bounded: the target lies at most nch * spacing cycles after c0
+            while (clock64() - c0 < c * spacing) __nanosleep(128);
+        }
         uint32_t v[2][32];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
@@ -553,7 +564,7 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
             fence_after();
             unsigned long long* te = &ctl->tempty[acc];
             drain_accumulator(tmem + acc * ACC_COLS, q, lane, rb * (BM / 2), row_scale, H,
-                              prm.A, prm.lags.ldH, BN, col0, valid, [&] {
+                              prm.A, prm.lags.ldH, BN, col0, valid, prm.epi_spacing, [&] {
                                   fence_before();
                                   __syncwarp();
                                   if (lane == 0) mbar_arrive(te);
@@ -827,7 +838,7 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
             fence_after();
             unsigned long long* te = &ctl->tempty[acc];
             drain_accumulator(tmem + acc * ACC_COLS, q, lane, rb * (BM / 2), row_scale, H,
-                              prm.A, prm.lags.ldH, BN, col0, valid, [&] {
+                              prm.A, prm.lags.ldH, BN, col0, valid, prm.epi_spacing, [&] {
                                   fence_before();
                                   __syncwarp();
                                   if (lane == 0) {
@@ -915,6 +926,13 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     prm.num_kb = (N + F::BK - 1) / F::BK;
     prm.wait_limit_ns = wait_limit_ns();
     prm.err = h->status_dev;
+    // a tile's products take ~num_kb * 4 MMAs of BN/2 cycles (M = 128, any operand type);
+    // the epilogue's chunks are spread over EPI_SPREAD of that
+    {
+        const long long nch = (prm.BN + 63) / 64;
+        const long long tile_cycles = (long long)prm.num_kb * 2LL * prm.BN;
+        prm.epi_spacing = nch > 1 ? (long long)(EPI_SPREAD * (double)tile_cycles) / nch : 0;
+    }
 
     long long grid = h->num_sms;
     if (grid >= prm.num_jt) grid = grid / prm.num_jt * prm.num_jt;
