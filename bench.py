@@ -221,6 +221,70 @@ def max_over_ranks(ms: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def run_yardsticks(dev, bits, Y, pilot, K, L, taps_per_step, reps: int = 20):
+    """O(N log N) alternatives on the same batch, for comparison only (not the paper's
+    method): the library's fast m-sequence transform (permutation + Walsh-Hadamard, FP32,
+    HBM-bound: 8 B read per sample, 8 B written per lag) and a cuFFT circular correlation
+    through torch.fft.  Each reports ms per batch and its NMSE against the library's FP32
+    SIMT estimate of the same batch."""
+    import torch
+
+    import paper_2206_05506_gb300 as pk
+    F, M, N = Y.shape
+    KL = K * L
+    peaks, _ = load_peaks()
+    out = {}
+    H32 = pk.estimate(Y, pilot, K, L, dtype="fp32")
+
+    def nmse(a):
+        return float(((a - H32).abs() ** 2).sum().item() / (H32.abs() ** 2).sum().item())
+
+    fmt = pk.FmtPilot(bits, device=dev)
+    Hf = torch.empty_like(H32)
+    pk.trace_enable(True, dev)
+    for _ in range(3):
+        pk.estimate_fmt(Y, fmt, K, L, out=Hf)
+    pk.trace_read(dev)
+    for _ in range(reps):
+        pk.estimate_fmt(Y, fmt, K, L, out=Hf)
+    ms = float(np.median([t for kind, t in pk.trace_read(dev) if kind == "fmt"]))
+    pk.trace_enable(False, dev)
+    gbs = (F * M * (8.0 * N + 8.0 * KL)) / (ms / 1e3) / 1e9
+    out["fast_msequence_transform"] = {
+        "ms_per_batch": ms, "value": taps_per_step / (ms / 1e3), "unit": "taps/s",
+        "achieved_gbs": gbs, "hbm_peak_gbs": peaks["hbm_gbs"],
+        "frac_hbm": gbs / peaks["hbm_gbs"], "nmse_vs_fp32_simt": nmse(Hf)}
+    del Hf, fmt
+    # cuFFT: H = ifft(fft(y) * conj(fft(p)))[:KL] / N, through torch (library FFTs)
+    p = torch.from_numpy(1.0 - 2.0 * bits.astype(np.float32)).to(dev)
+    Pc = torch.conj(torch.fft.fft(p.to(torch.complex64)))
+
+    def fft_corr():
+        c = torch.fft.ifft(torch.fft.fft(Y, dim=-1) * Pc, dim=-1)
+        return c[..., :KL]
+
+    for _ in range(2):
+        Hc = fft_corr()
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record()
+    n = 5
+    for _ in range(n):
+        Hc = fft_corr()
+    a1.record()
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / n
+    Hc = Hc.reshape(H32.shape) / N
+    out["cufft_circular_correlation"] = {
+        "ms_per_batch": ms, "value": taps_per_step / (ms / 1e3), "unit": "taps/s",
+        "nmse_vs_fp32_simt": nmse(Hc),
+        "note": "torch.fft (cuFFT) forward + inverse over all N lags, then the first K*L"}
+    del Hc, Pc, H32
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_differentiation(dev, steps: int = 20):
     """Relaxed-pilot forward + adjoint (dLoss/dY and dLoss/dtheta) on the differentiation
     workload (M=64, N=1023, K=8, L=64, 64 frames, FP32), as one training step would."""
@@ -318,6 +382,8 @@ def main():
                     help="length of the Poisson serving trace (0: skip)")
     ap.add_argument("--differentiation", type=int, default=1,
                     help="also time the relaxed-pilot forward + adjoint (1/0)")
+    ap.add_argument("--yardsticks", type=int, default=1,
+                    help="time the O(N log N) yardsticks (fast m-sequence transform, cuFFT)")
     ap.add_argument("--other-dtypes", type=int, default=1,
                     help="also time the other arithmetics on the same batch (1/0)")
     args = ap.parse_args()
@@ -511,6 +577,8 @@ def main():
             del ows
         assert pk.get_status(dev) == 0
 
+    yard = run_yardsticks(dev, bits, Y, pilot, K, L, taps_per_step) if args.yardsticks else None
+
     line = {
         "metric": "CIR taps estimated/s", "value": value, "unit": "taps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -540,6 +608,7 @@ def main():
         "serving": serving,
         "other_dtypes": others,
         "differentiation": differentiation,
+        "yardsticks": yard,
     }
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -272,6 +272,33 @@ pnce_status pnce_estimate_static(pnce_handle* h, const pnce_pilot* pilot, const 
                                  int F, int M, int N, int K, int L, int dtype, void* H_dev,
                                  void* stream);
 
+/*
+ * Fast m-sequence transform: a yardstick beside the paper's method, not part of it (the
+ * paper correlates with the dense circulant, Sec. III-B).  For an m-sequence pilot of
+ * degree r (N = 2^r - 1) the same estimate, H[f][m][k][l] = (1/N) sum_n Y[f][m][n]
+ * p[(n - l - kL) mod N], is a permutation of each received row into a vector of 2^r
+ * entries, a Walsh-Hadamard transform and a gather of the K*L lags: O(N log N) per row
+ * instead of O(N K L), in FP32 on the CUDA cores.
+ *
+ * pnce_fmt_tables (host only, no device use): for bits_host packed as for
+ * pnce_pilot_create, fills pos[n] (n < N) with the r-bit window
+ * s_n = sum_{i<r} bit[(n+i) mod N] 2^i and lagvec[j] (j < N) with the vector u_j for which
+ * bit[(n - j) mod N] = parity(u_j & s_n) for every n.  Both arrays are caller-owned,
+ * N entries each.  Returns PNCE_EINVAL unless N = 2^r - 1 with 2 <= r <= 14 and the bits
+ * are an m-sequence (distinct nonzero windows, and the order-r linear recurrence they
+ * imply holds over the whole period).
+ * pnce_fmt_create builds the tables and uploads them to the handle's device (synchronous);
+ * pnce_fmt_destroy frees them.
+ * pnce_estimate_fmt: Y_dev complex64 [F][M][N], H_dev complex64 [F][M][K][L] (fully
+ * overwritten), K*L <= N, both 16-byte aligned; enqueued on `stream`, no workspace.
+ */
+typedef struct pnce_fmt pnce_fmt;
+pnce_status pnce_fmt_tables(const uint32_t* bits_host, int N, uint16_t* pos, uint16_t* lagvec);
+pnce_status pnce_fmt_create(pnce_handle* h, const uint32_t* bits_host, int N, pnce_fmt** out);
+pnce_status pnce_fmt_destroy(pnce_fmt* f);
+pnce_status pnce_estimate_fmt(pnce_handle* h, const pnce_fmt* f, const void* Y_dev, int F,
+                              int M, int N, int K, int L, void* H_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,7 +99,7 @@ def trace_enable(on: bool = True, device=None):
     check(lib().pnce_trace_enable(ctx.handle, 1 if on else 0), "pnce_trace_enable")
 
 
-TRACE_KINDS = {0: "quantize", 1: "correlate", 2: "simt"}
+TRACE_KINDS = {0: "quantize", 1: "correlate", 2: "simt", 3: "fmt"}
 
 
 def trace_read(device=None, max_entries: int = 8192):
@@ -122,16 +122,7 @@ class Pilot:
     """Device-resident m-sequence pilot (bits 0/1, bit 0 -> +1, bit 1 -> -1)."""
 
     def __init__(self, bits, device=None):
-        b = np.asarray(bits.cpu().numpy() if isinstance(bits, torch.Tensor) else bits)
-        b = b.astype(np.uint8).ravel()
-        if b.size < 2 or np.any(b > 1):
-            raise ValueError("pilot bits must be a 0/1 array of length >= 2")
-        self.N = int(b.size)
-        nw = (self.N + 31) // 32
-        padded = np.zeros(nw * 32, dtype=np.uint64)
-        padded[: self.N] = b
-        words = (padded.reshape(nw, 32) << np.arange(32, dtype=np.uint64)).sum(axis=1)
-        self.words = np.ascontiguousarray(words.astype(np.uint32))
+        self.N, self.words = _pack_bits(bits)
         self.ctx = context(device)
         self.device = self.ctx.device
         p = C.c_void_p()
@@ -150,6 +141,70 @@ class Pilot:
         if p is not None and _lib._lib is not None:
             _lib._lib.pnce_pilot_destroy(p)
             self._p = None
+
+
+def _pack_bits(bits) -> tuple[int, np.ndarray]:
+    b = np.asarray(bits.cpu().numpy() if isinstance(bits, torch.Tensor) else bits)
+    b = b.astype(np.uint8).ravel()
+    if b.size < 2 or np.any(b > 1):
+        raise ValueError("pilot bits must be a 0/1 array of length >= 2")
+    nw = (b.size + 31) // 32
+    padded = np.zeros(nw * 32, dtype=np.uint64)
+    padded[: b.size] = b
+    words = (padded.reshape(nw, 32) << np.arange(32, dtype=np.uint64)).sum(axis=1)
+    return int(b.size), np.ascontiguousarray(words.astype(np.uint32))
+
+
+def fmt_tables(bits):
+    """(pos, lagvec) uint16 arrays of the fast m-sequence transform (host only): the r-bit
+    window s_n of every sample n and the vector u_j of every lag j, with
+    bit[(n - j) mod N] = parity(u_j & s_n).  Raises PnceError unless bits is an m-sequence."""
+    N, words = _pack_bits(bits)
+    pos = np.zeros(N, dtype=np.uint16)
+    lag = np.zeros(N, dtype=np.uint16)
+    check(lib().pnce_fmt_tables(words.ctypes.data_as(C.POINTER(C.c_uint32)), N,
+                                pos.ctypes.data_as(C.POINTER(C.c_uint16)),
+                                lag.ctypes.data_as(C.POINTER(C.c_uint16))), "pnce_fmt_tables")
+    return pos, lag
+
+
+class FmtPilot:
+    """Device tables of the fast m-sequence transform (a yardstick, not the paper's method)."""
+
+    def __init__(self, bits, device=None):
+        self.N, words = _pack_bits(bits)
+        self.ctx = context(device)
+        self.device = self.ctx.device
+        p = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().pnce_fmt_create(self.ctx.handle,
+                                        words.ctypes.data_as(C.POINTER(C.c_uint32)), self.N,
+                                        C.byref(p)), "pnce_fmt_create")
+        self._p = p
+
+    @property
+    def handle(self):
+        return self._p
+
+    def __del__(self):
+        p = getattr(self, "_p", None)
+        if p is not None and _lib._lib is not None:
+            _lib._lib.pnce_fmt_destroy(p)
+            self._p = None
+
+
+def estimate_fmt(Y: torch.Tensor, fmt: "FmtPilot", K: int, L: int, out=None) -> torch.Tensor:
+    """The estimate by the fast m-sequence transform (FP32, CUDA cores): same H as
+    estimate(), computed in O(N log N) per row."""
+    F, M, N = _check_y(Y)
+    if N != fmt.N:
+        raise ValueError("Y's N differs from the transform's")
+    dev = Y.device
+    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    with torch.cuda.device(dev):
+        check(lib().pnce_estimate_fmt(fmt.ctx.handle, fmt.handle, Y.data_ptr(), F, M, N, K, L,
+                                      H.data_ptr(), _stream(dev)), "pnce_estimate_fmt")
+    return H
 
 
 def workspace_size(F, M, N, K, L, dtype) -> int:

@@ -51,6 +51,11 @@ _SIGS = {
     "pnce_host_workspace_size": (_sz, [_i, _i, _i, _i, _i, _i]),
     "pnce_estimate_host": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
     "pnce_estimate_static": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp]),
+    "pnce_fmt_tables": (_i, [C.POINTER(C.c_uint32), _i, C.POINTER(C.c_uint16),
+                             C.POINTER(C.c_uint16)]),
+    "pnce_fmt_create": (_i, [_vp, C.POINTER(C.c_uint32), _i, C.POINTER(_vp)]),
+    "pnce_fmt_destroy": (_i, [_vp]),
+    "pnce_estimate_fmt": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _vp, _vp]),
     "pnce_trace_enable": (_i, [_vp, _i]),
     "pnce_trace_read": (_i, [_vp, _vp, _vp, _i, C.POINTER(C.c_int)]),
     "pnce_gather_rows": (_i, [_vp, _i, _i, _vp, C.c_longlong, _vp]),

@@ -36,7 +36,7 @@ struct pnce_handle {
 
 namespace pnce {
 constexpr int kTraceMax = 8192;
-enum TraceKind { TRACE_QUANTIZE = 0, TRACE_CORRELATE = 1, TRACE_SIMT = 2 };
+enum TraceKind { TRACE_QUANTIZE = 0, TRACE_CORRELATE = 1, TRACE_SIMT = 2, TRACE_FMT = 3 };
 // Records a start event before / an end event after one kernel launch when tracing is on.
 struct TraceScope {
     pnce_handle* h;
