@@ -105,7 +105,7 @@ fmt_kernel(const float2* __restrict__ Y, long long A, int N, int r,
 // in one more pass over groups of entries 512 apart.  Every shared-memory access of the
 // passes is 32 consecutive entries per warp instruction.
 template <int R>
-__global__ void __launch_bounds__(THREADS)
+__global__ void __launch_bounds__(THREADS, R >= 14 ? 3 : 4)   // 4 rows in flight per SM
 fmt_kernel_seg(const float2* __restrict__ Y, long long A, int N,
                const uint16_t* __restrict__ pos, const uint16_t* __restrict__ lagvec, int KL,
                float invN, float2* __restrict__ H) {

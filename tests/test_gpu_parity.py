@@ -219,3 +219,14 @@ def test_invalid_arguments(pk):
                            ws.data_ptr(), 16, H.data_ptr(), None)
     assert st == 1                                          # workspace too small
     assert pk.get_status(dev) == 0
+
+
+@pytest.mark.parametrize("dtype", TC)
+def test_long_sequence_staged_pilot(pk, dtype):
+    # N = 16383: the pilot list of all K blocks no longer fits beside the pipeline, so the
+    # kernel takes the per-stage pilot generator on its own (256 K blocks of fp16)
+    r, M, K, L, F = 14, 9, 4, 256, 1
+    bits, _, Y = _case(r, M, K, L, F, seed=2)
+    H = _run(pk, Y, bits, K, L, dtype)
+    refq = O.estimate_quantized(Y, bits, K, L, dtype)
+    assert O.nmse(H, refq) <= TOL_Q[dtype]
