@@ -40,11 +40,11 @@ pnce_status from_cuda(cudaError_t e) { return e == cudaSuccess ? PNCE_OK : PNCE_
 // Frame chunks for pnce_estimate.  Off by default: the quantiser of a batch runs, then the
 // tensor-core correlation.  PNCE_OVERLAP_CHUNKS=n (2..8) splits a large batch into n frame
 // chunks and quantises chunk i+1 on one handle stream while chunk i is correlated on
-// another.  Measured on GB300 (512 x 128 x 4095, fp16, with an earlier correlation
-// kernel): 1.716 ms per estimate sequential, 1.743 / 1.653 / 1.650 / 1.798 / 1.691 ms with
-// 2 / 3 / 4 / 6 / 8 chunks -- the quantiser and the correlation compete for the SMs'
-// L1/shared-memory data path, so overlapping buys at most 4 %, and only when each chunk
-// keeps >= 8 waves of 128 x 256 tiles.  Chunks must hold whole 8-antenna operand groups.
+// another.  Measured on GB300 (512 x 128 x 4095, fp16): 1.460 ms per estimate
+// sequential, 1.493 / 1.440 / 1.431 / 1.567 ms with 2 / 3 / 4 / 6 chunks -- the quantiser
+// and the correlation compete for the SMs' L1/shared-memory data path, so overlapping buys
+// at most 2 %, and only when each chunk keeps >= 8 waves of 128 x 256 tiles.  Chunks must
+// hold whole 8-antenna operand groups.
 int estimate_chunks(const pnce_handle* h, int F, int M, int N, int KL) {
     (void)N;
     const char* e = getenv("PNCE_OVERLAP_CHUNKS");
