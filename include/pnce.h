@@ -208,8 +208,11 @@ pnce_status pnce_backward(pnce_handle* h, const float* pilot_dev, int pilot_map,
  * pipeline starts after the work already queued on `stream`, and `stream` waits for its
  * end: to the caller the call behaves as if it were enqueued on `stream`.  All device
  * buffers live in workspace_dev (pnce_host_workspace_size bytes, caller-owned).  Host
- * buffers should be page-locked for the copies to be asynchronous.  Calls on the same
- * handle are serialised on the handle's pipeline streams.
+ * buffers should be page-locked for the copies to be asynchronous.  Y comes in by
+ * cudaMemcpyAsync; H goes out by a copy kernel storing into H_host when H_host is
+ * page-locked memory known to CUDA (it shares the host link with the inbound copy better
+ * than a second DMA does), by cudaMemcpyAsync otherwise.  Calls on the same handle are
+ * serialised on the handle's pipeline streams.
  */
 size_t pnce_host_workspace_size(int F, int M, int N, int K, int L, int dtype);
 pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const void* Y_host,

@@ -523,6 +523,20 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
     if (dtype != PNCE_FP32_SIMT && !(h->cc_major == 10 && h->cc_minor == 3))
         return PNCE_EUNSUPPORTED;
 
+    // copy-out: into page-locked H_host by a kernel (it shares the host link with the
+    // copy-in DMA better than a second DMA does); into pageable memory by cudaMemcpyAsync
+    unsigned char* h_mapped = nullptr;
+    {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, H_host) == cudaSuccess) {
+            if (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr &&
+                ((uintptr_t)at.devicePointer & 7u) == 0)
+                h_mapped = static_cast<unsigned char*>(at.devicePointer);
+        } else {
+            cudaGetLastError();                  // unknown pointer: take the copy path
+        }
+    }
+
     std::lock_guard<std::recursive_mutex> guard(h->lock);   // uses the handle's streams
     cudaStream_t user = static_cast<cudaStream_t>(stream);
     unsigned char* ws = static_cast<unsigned char*>(workspace_dev);
@@ -569,10 +583,13 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
         if (st != PNCE_OK) return st;
         if (cudaEventRecord(h->ev_comp[b], h->s_comp) != cudaSuccess) return PNCE_ECUDA;
         // copy-out
-        if (cudaStreamWaitEvent(h->s_d2h, h->ev_comp[b], 0) != cudaSuccess ||
-            cudaMemcpyAsync(hh + (size_t)f0 * frame_h, hd, (size_t)fc * frame_h,
-                            cudaMemcpyDeviceToHost, h->s_d2h) != cudaSuccess ||
-            cudaEventRecord(h->ev_out[b], h->s_d2h) != cudaSuccess)
+        if (cudaStreamWaitEvent(h->s_d2h, h->ev_comp[b], 0) != cudaSuccess) return PNCE_ECUDA;
+        const cudaError_t ce =
+            h_mapped ? pnce::launch_copy_to_host(hd, h_mapped + (size_t)f0 * frame_h,
+                                                 (size_t)fc * frame_h, h->num_sms, h->s_d2h)
+                     : cudaMemcpyAsync(hh + (size_t)f0 * frame_h, hd, (size_t)fc * frame_h,
+                                       cudaMemcpyDeviceToHost, h->s_d2h);
+        if (ce != cudaSuccess || cudaEventRecord(h->ev_out[b], h->s_d2h) != cudaSuccess)
             return PNCE_ECUDA;
     }
     // the caller's stream resumes when all three pipeline streams are done

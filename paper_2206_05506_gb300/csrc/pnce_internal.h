@@ -158,5 +158,10 @@ cudaError_t launch_backward(const float* p, bool tanh_map, const float2* Y, cons
 cudaError_t launch_adjoint_dy(const float* p, bool tanh_map, const float2* G, long long A, int N,
                               int KL, float2* dY, cudaStream_t s);
 size_t backward_workspace(long long A, int N, int KL);
+// copy `bytes` (a multiple of 8) from device memory into page-locked host memory with a
+// kernel of at most num_sms blocks; dst must be the device-visible address of the
+// page-locked buffer
+cudaError_t launch_copy_to_host(const void* src_dev, void* dst_host_mapped, size_t bytes,
+                                int num_sms, cudaStream_t s);
 
 }  // namespace pnce

@@ -3,7 +3,11 @@
 // estimate.  These kernels move rows between per-antenna addresses (typically page-locked
 // host memory, read and written by the GPU directly over the host link) and the batch's
 // contiguous device buffers, so a whole batch needs no per-request copy calls and its
-// launch sequence can be captured once and replayed.
+// launch sequence can be captured once and replayed.  The contiguous copy-out kernel serves
+// pnce_estimate_host: stores from the SMs into page-locked host memory share the host link
+// with a concurrent host-to-device DMA better than a device-to-host DMA does (measured on
+// GB300: 2.15 GB in and 1.07 GB out together in 10.6 ms against 11.3 ms with two DMAs; the
+// inbound copy alone takes 10.15 ms).
 #include "pnce_internal.h"
 
 namespace {
@@ -37,7 +41,30 @@ scatter_rows_kernel(const float2* __restrict__ src, long long src_pitch,
     for (int i = threadIdx.x; i < n; i += THREADS) d[i] = s[i];
 }
 
+// dst[0 .. n) = src[0 .. n) (8-byte elements), grid-stride; dst is page-locked host memory
+__global__ void __launch_bounds__(THREADS)
+copy_out_kernel(const float2* __restrict__ src, float2* dst, long long n) {
+    const long long stride = (long long)gridDim.x * THREADS;
+    for (long long i = blockIdx.x * (long long)THREADS + threadIdx.x; i < n; i += stride)
+        dst[i] = __ldcs(src + i);
+}
+
 }  // namespace
+
+namespace pnce {
+
+cudaError_t launch_copy_to_host(const void* src_dev, void* dst_host_mapped, size_t bytes,
+                                int num_sms, cudaStream_t s) {
+    const long long n = (long long)(bytes / sizeof(float2));
+    if (n <= 0) return cudaSuccess;
+    long long grid = (n + THREADS - 1) / THREADS;
+    if (grid > num_sms) grid = num_sms;
+    copy_out_kernel<<<(unsigned)grid, THREADS, 0, s>>>(static_cast<const float2*>(src_dev),
+                                                       static_cast<float2*>(dst_host_mapped), n);
+    return cudaGetLastError();
+}
+
+}  // namespace pnce
 
 extern "C" {
 
