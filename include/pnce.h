@@ -203,7 +203,7 @@ pnce_status pnce_backward(pnce_handle* h, const float* pilot_dev, int pilot_map,
  * End-to-end estimate from host memory (the paper's frame latency includes the host to
  * device transfer, Sec. IV-C): copies Y_host (complex64 [F][M][N]) to the device,
  * estimates as pnce_estimate, and copies H back to H_host (complex64 [F][M][K][L]).
- * Frames go through in chunks, double buffered, on three streams owned by the handle
+ * Frames go through in chunks, triple buffered, on three streams owned by the handle
  * (copy-in, kernels, copy-out), so both copy directions overlap the kernels.  The
  * pipeline starts after the work already queued on `stream`, and `stream` waits for its
  * end: to the caller the call behaves as if it were enqueued on `stream`.  All device

@@ -157,7 +157,7 @@ pnce_status pnce_create(pnce_handle** out) {
     ok = ok && cudaEventCreateWithFlags(&h->ev_est_start, ef) == cudaSuccess;
     for (int i = 0; i < 2 && ok; ++i)
         ok = ok && cudaEventCreateWithFlags(&h->ev_est_done[i], ef) == cudaSuccess;
-    for (int i = 0; i < 2 && ok; ++i) {
+    for (int i = 0; i < kPnceHostSlots && ok; ++i) {
         ok = ok && cudaEventCreateWithFlags(&h->ev_in[i], ef) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&h->ev_comp[i], ef) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&h->ev_out[i], ef) == cudaSuccess;
@@ -182,7 +182,7 @@ pnce_status pnce_destroy(pnce_handle* h) {
     if (h->ev_est_start) cudaEventDestroy(h->ev_est_start);
     for (int i = 0; i < 2; ++i)
         if (h->ev_est_done[i]) cudaEventDestroy(h->ev_est_done[i]);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < kPnceHostSlots; ++i)
         for (cudaEvent_t e : {h->ev_in[i], h->ev_comp[i], h->ev_out[i]})
             if (e) cudaEventDestroy(e);
     if (h->ev_start) cudaEventDestroy(h->ev_start);
@@ -466,19 +466,20 @@ pnce_status pnce_backward(pnce_handle* h, const float* p_dev, int pilot_map, con
 
 namespace {
 
-// Host pipeline layout: frames go through in chunks of fc frames, two slots of
-// (Y chunk, H chunk) so that copy-in of chunk i+1 and copy-out of chunk i-1 overlap the
-// kernels of chunk i, plus the quantisation workspace of one chunk.
+// Host pipeline layout: frames go through in chunks of fc frames, kPnceHostSlots slots of
+// (Y chunk, H chunk) so that copy-in of the next chunks and copy-out of the previous ones
+// overlap the kernels of chunk i without waiting on each other slot by slot, plus the
+// quantisation workspace of one chunk.
 struct HostLayout {
     int fc;                        // frames per chunk
     size_t y_bytes, h_bytes;       // per slot
-    size_t y_off[2], h_off[2], q_off, total;
+    size_t y_off[kPnceHostSlots], h_off[kPnceHostSlots], q_off, total;
 };
 
 HostLayout host_layout(int F, int M, int N, int K, int L, int dtype) {
     HostLayout l{};
     const size_t frame_y = (size_t)M * N * 8;
-    const size_t target = (size_t)128 << 20;       // ~128 MB of Y per chunk
+    const size_t target = (size_t)64 << 20;        // ~64 MB of Y per chunk
     long long fc = (long long)((target + frame_y - 1) / frame_y);
     const long long min_chunks = 4;                // enough chunks to overlap copy and compute
     if ((F + fc - 1) / fc < min_chunks) fc = (F + min_chunks - 1) / min_chunks;
@@ -488,7 +489,7 @@ HostLayout host_layout(int F, int M, int N, int K, int L, int dtype) {
     l.y_bytes = pnce::round_up((size_t)fc * frame_y, 256);
     l.h_bytes = pnce::round_up((size_t)fc * M * (size_t)K * L * 8, 256);
     size_t off = 0;
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kPnceHostSlots; ++b) {
         l.y_off[b] = off;
         off += l.y_bytes;
         l.h_off[b] = off;
@@ -550,20 +551,20 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
         if (cudaStreamWaitEvent(s, h->ev_start, 0) != cudaSuccess) return PNCE_ECUDA;
 
     for (int f0 = 0, i = 0; f0 < F; f0 += lay.fc, ++i) {
-        const int b = i & 1;
+        const int b = i % kPnceHostSlots;
         const int fc = (F - f0 < lay.fc) ? (F - f0) : lay.fc;
         void* yd = ws + lay.y_off[b];
         void* hd = ws + lay.h_off[b];
-        // copy-in: slot b is free once the kernels of chunk i-2 have read it
-        if (i >= 2 && cudaStreamWaitEvent(h->s_h2d, h->ev_comp[b], 0) != cudaSuccess)
+        // copy-in: slot b is free once the kernels of its previous chunk have read it
+        if (i >= kPnceHostSlots && cudaStreamWaitEvent(h->s_h2d, h->ev_comp[b], 0) != cudaSuccess)
             return PNCE_ECUDA;
         if (cudaMemcpyAsync(yd, yh + (size_t)f0 * frame_y, (size_t)fc * frame_y,
                             cudaMemcpyHostToDevice, h->s_h2d) != cudaSuccess ||
             cudaEventRecord(h->ev_in[b], h->s_h2d) != cudaSuccess)
             return PNCE_ECUDA;
-        // kernels: need the input, and H slot b drained by the copy-out of chunk i-2
+        // kernels: need the input, and H slot b drained by the copy-out of its previous chunk
         if (cudaStreamWaitEvent(h->s_comp, h->ev_in[b], 0) != cudaSuccess) return PNCE_ECUDA;
-        if (i >= 2 && cudaStreamWaitEvent(h->s_comp, h->ev_out[b], 0) != cudaSuccess)
+        if (i >= kPnceHostSlots && cudaStreamWaitEvent(h->s_comp, h->ev_out[b], 0) != cudaSuccess)
             return PNCE_ECUDA;
         const long long A = (long long)fc * M;
         if (dtype == PNCE_FP32_SIMT) {

@@ -9,6 +9,9 @@
 
 #include "pnce.h"
 
+// chunk slots of the host-buffer pipeline (pnce_estimate_host)
+constexpr int kPnceHostSlots = 3;
+
 struct pnce_handle {
     int device;
     int num_sms;
@@ -18,7 +21,8 @@ struct pnce_handle {
     // host-buffer pipeline (pnce_estimate_host): copy-in, compute and copy-out streams,
     // and per double-buffer slot events
     cudaStream_t s_h2d, s_comp, s_d2h;
-    cudaEvent_t ev_in[2], ev_comp[2], ev_out[2], ev_start, ev_done[3];
+    cudaEvent_t ev_in[kPnceHostSlots], ev_comp[kPnceHostSlots], ev_out[kPnceHostSlots];
+    cudaEvent_t ev_start, ev_done[3];
     // pnce_estimate on large batches: quantisation of frame chunk i+1 (s_quant) overlaps
     // the tensor-core correlation of chunk i (s_corr)
     cudaStream_t s_quant, s_corr;
