@@ -246,6 +246,37 @@ pnce_status pnce_trace_read(pnce_handle* h, int* kinds, float* ms, int max_entri
  * pnce_scatter_rows: dst_rows[r][0..counts[r]) = src_dev[r][0..counts[r]) for r < rows,
  *   source row pitch src_pitch elements (counts are clamped to src_pitch).
  */
+/*
+ * Grouped estimate for serving (§ continuous batching; the paper processes one frame at a
+ * time, so this has no counterpart there): the antennas of nreq requests that share one
+ * pilot (same N) are estimated as one batch of `rows` rows with kl_max lags.  descs is a
+ * table of nreq <= rows descriptors in device memory or page-locked host memory, copied
+ * to the workspace by the call's first operation (a copy node when captured, so the table
+ * can be rewritten between replays of a captured graph).  Request b moves its
+ * received rows Y (complex64 [M][N]) into batch rows row_offset .. row_offset+M-1 (the
+ * requests' row ranges must not overlap), and
+ * gets back H (complex64 [M][K*L]) = the first K*L lags of those rows, with lag
+ * j = k*L + l as in pnce_estimate.  Y and H may be device memory or page-locked host
+ * memory (read and written by the GPU over the host link).  M = 0 marks an empty slot.  A
+ * descriptor with row_offset + M > rows, K*L > kl_max or a NULL buffer is skipped and
+ * latches PNCE_EINVAL (pnce_get_status).  Batch rows no request covers are estimated from
+ * whatever the workspace holds and discarded.  workspace_dev: 256-byte aligned,
+ * pnce_grouped_workspace_size(rows, N, kl_max, dtype) bytes (0 for invalid shapes).
+ * Enqueues gather, quantiser (tensor-core dtypes), correlation and scatter kernels on
+ * `stream`; allocates nothing.
+ */
+typedef struct {
+    const void* Y;          /* complex64 [M][N] */
+    void* H;                /* complex64 [M][K*L] */
+    int M, K, L;
+    int row_offset;         /* first batch row of the request */
+} pnce_req_desc;
+size_t pnce_grouped_workspace_size(int rows, int N, int kl_max, int dtype);
+pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
+                                  const pnce_req_desc* descs, int nreq, int rows, int kl_max,
+                                  int dtype, void* workspace_dev, size_t workspace_bytes,
+                                  void* stream);
+
 pnce_status pnce_gather_rows(const uint64_t* src_rows, int rows, int nelem, void* dst_dev,
                              long long dst_pitch, void* stream);
 pnce_status pnce_scatter_rows(const void* src_dev, long long src_pitch, const uint64_t* dst_rows,

@@ -211,6 +211,23 @@ def workspace_size(F, M, N, K, L, dtype) -> int:
     return int(lib().pnce_workspace_size(F, M, N, K, L, _dt(dtype)))
 
 
+def grouped_workspace_size(rows, N, kl_max, dtype) -> int:
+    return int(lib().pnce_grouped_workspace_size(rows, N, kl_max, _dt(dtype)))
+
+
+def estimate_grouped(pilot: "Pilot", descs_ptr: int, nreq: int, rows: int, kl_max: int, dtype,
+                     workspace: torch.Tensor, stream=None):
+    """Grouped estimate (pnce_estimate_grouped): descs_ptr is the address of nreq
+    pnce_req_desc entries (_lib.ReqDesc) that the GPU can read (device or page-locked
+    host memory); each request's Y and H buffers likewise.  Enqueues only."""
+    dev = pilot.device
+    with torch.cuda.device(dev):
+        s = _stream(dev) if stream is None else stream
+        check(lib().pnce_estimate_grouped(pilot.ctx.handle, pilot.handle, descs_ptr, nreq, rows,
+                                          kl_max, _dt(dtype), workspace.data_ptr(),
+                                          workspace.numel(), s), "pnce_estimate_grouped")
+
+
 def backward_workspace_size(F, M, N, K, L) -> int:
     return int(lib().pnce_backward_workspace_size(F, M, N, K, L))
 

@@ -27,6 +27,12 @@ _lib = None
 _vp, _i, _sz = C.c_void_p, C.c_int, C.c_size_t
 
 
+class ReqDesc(C.Structure):
+    """pnce_req_desc: one request of a grouped estimate."""
+    _fields_ = [("Y", C.c_void_p), ("H", C.c_void_p), ("M", C.c_int), ("K", C.c_int),
+                ("L", C.c_int), ("row_offset", C.c_int)]
+
+
 class FrameOpts(C.Structure):
     """pnce_frame_opts"""
     _fields_ = [("cp_len", C.c_int), ("shift_rule", C.c_int)]
@@ -51,6 +57,8 @@ _SIGS = {
     "pnce_host_workspace_size": (_sz, [_i, _i, _i, _i, _i, _i]),
     "pnce_estimate_host": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _sz, _vp, _vp]),
     "pnce_estimate_static": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _i, _i, _vp, _vp]),
+    "pnce_grouped_workspace_size": (_sz, [_i, _i, _i, _i]),
+    "pnce_estimate_grouped": (_i, [_vp, _vp, _vp, _i, _i, _i, _i, _vp, _sz, _vp]),
     "pnce_fmt_tables": (_i, [C.POINTER(C.c_uint32), _i, C.POINTER(C.c_uint16),
                              C.POINTER(C.c_uint16)]),
     "pnce_fmt_create": (_i, [_vp, C.POINTER(C.c_uint32), _i, C.POINTER(_vp)]),

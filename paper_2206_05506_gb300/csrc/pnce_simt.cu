@@ -42,6 +42,7 @@ struct Smem {
     float e[2][EPAD];
     float2 y[2][TA][NC];
 };
+static_assert(offsetof(Smem, y) % 16 == 0 && NC % 2 == 0, "paired sample loads need 16-byte rows");
 
 // FWD_BITS: +-1 pilot from packed bits.  FWD_REAL / ADJ_REAL: float pilot, read forwards
 // or backwards.  *_TANH: the float argument is theta and the pilot is tanh(theta).
@@ -120,23 +121,30 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
 #pragma unroll
         for (int i = 0; i < 15; ++i) w[i] = e[epos(base - 7 + i)];
 
-#pragma unroll 1
+#pragma unroll 2   // the sliding window's shifts become register renames
         for (int s = 0; s < NC / 8; ++s) {
             float nw[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) nw[i] = e[epos(8 * s + 8 + base + i)];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                float2 y[RA];
+            for (int u2 = 0; u2 < 8; u2 += 2) {
+                // two consecutive samples per 16-byte load (rows of sm.y are 16-byte aligned)
+                float4 yy[RA];
 #pragma unroll
-                for (int i = 0; i < RA; ++i) y[i] = sm.y[buf][warp * RA + i][8 * s + u];
+                for (int i = 0; i < RA; ++i)
+                    yy[i] = *reinterpret_cast<const float4*>(&sm.y[buf][warp * RA + i][8 * s + u2]);
 #pragma unroll
-                for (int r = 0; r < RJ; ++r) {
-                    const float pv = w[u - r + 7];
+                for (int h = 0; h < 2; ++h) {
+                    const int u = u2 + h;
 #pragma unroll
-                    for (int i = 0; i < RA; ++i) {
-                        acc[i][r].x = fmaf(pv, y[i].x, acc[i][r].x);
-                        acc[i][r].y = fmaf(pv, y[i].y, acc[i][r].y);
+                    for (int r = 0; r < RJ; ++r) {
+                        const float pv = w[u - r + 7];
+#pragma unroll
+                        for (int i = 0; i < RA; ++i) {
+                            const float yx = h ? yy[i].z : yy[i].x, yi = h ? yy[i].w : yy[i].y;
+                            acc[i][r].x = fmaf(pv, yx, acc[i][r].x);
+                            acc[i][r].y = fmaf(pv, yi, acc[i][r].y);
+                        }
                     }
                 }
             }

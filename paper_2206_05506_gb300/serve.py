@@ -11,9 +11,10 @@ taps) whose received blocks sit in page-locked host memory.  The loop
   other batches are on the GPU join the next batch, and up to `slots` batches run
   concurrently on their own streams;
 * runs each batch as one replay of a CUDA graph captured once per (slot, N, lag class,
-  capacity): gather the requests' antenna rows from host memory into the batch buffer,
-  estimate (quantise + tensor-core correlation, or the FP32 SIMT path), scatter each
-  antenna's lags straight into its request's host result buffer;
+  capacity) around one pnce_estimate_grouped call: from a descriptor table in page-locked
+  host memory it gathers the requests' antenna rows from host memory into the batch
+  buffer, estimates (quantise + tensor-core correlation, or the FP32 SIMT path) and
+  scatters each antenna's lags straight into its request's host result buffer;
 * polls the batches' events and stamps each request's completion; latency is completion
   minus scheduled arrival.
 
@@ -24,13 +25,14 @@ the same alone and in any mix.
 from __future__ import annotations
 
 import collections
+import ctypes as C
 import time
 from dataclasses import dataclass
 
 import numpy as np
 import torch
 
-from . import DTYPES, Pilot, check, context, lib, workspace_size
+from . import DTYPES, Pilot, _lib, context, estimate_grouped, grouped_workspace_size
 
 KL_CLASSES = (64, 256, 1024)
 CAPACITIES = (64, 256, 1024, 4096)        # antennas per batch
@@ -184,15 +186,15 @@ class _Shape:
     def __init__(self, eng: "GpuEngine", slot: int, N: int, klc: int, cap: int):
         dev = eng.device
         self.N, self.klc, self.cap = N, klc, cap
-        self.Y = torch.zeros((1, cap, N), dtype=torch.complex64, device=dev)
-        self.H = torch.zeros((1, cap, 1, klc), dtype=torch.complex64, device=dev)
-        need = workspace_size(1, cap, N, 1, klc, eng.dt)
-        self.ws = torch.empty(max(need, 256), dtype=torch.uint8, device=dev)
-        # descriptor tables in page-locked host memory: the kernels read them directly
-        self.src = torch.zeros(cap, dtype=torch.int64, pin_memory=True)
-        self.dst = torch.zeros(cap, dtype=torch.int64, pin_memory=True)
-        self.cnt = torch.zeros(cap, dtype=torch.int32, pin_memory=True)
-        self.src_np, self.dst_np, self.cnt_np = self.src.numpy(), self.dst.numpy(), self.cnt.numpy()
+        self.ws = torch.empty(grouped_workspace_size(cap, N, klc, eng.dtype), dtype=torch.uint8,
+                              device=dev)
+        # request descriptors (pnce_req_desc) in page-locked host memory: the kernels read
+        # them directly, so a captured graph picks up each batch's table
+        assert C.sizeof(_lib.ReqDesc) == 32
+        self.desc = torch.zeros(cap * 32, dtype=torch.uint8, pin_memory=True)
+        d = self.desc.numpy()
+        self.d_ptr = d.view(np.int64).reshape(cap, 4)      # Y, H
+        self.d_int = d.view(np.int32).reshape(cap, 8)      # [4] M, [5] K, [6] L, [7] row offset
         self.pilot = eng.pilot(N)
         self.graph = None
         stream = eng.streams[slot]
@@ -206,26 +208,18 @@ class _Shape:
             self.graph = g
 
     def _enqueue(self, eng: "GpuEngine", s: int):
-        L = lib()
-        check(L.pnce_gather_rows(self.src.data_ptr(), self.cap, self.N, self.Y.data_ptr(),
-                                 self.N, s), "pnce_gather_rows")
-        check(L.pnce_estimate(eng.ctx.handle, self.pilot.handle, self.Y.data_ptr(), 1, self.cap,
-                              self.N, 1, self.klc, eng.dt, self.ws.data_ptr(), self.ws.numel(),
-                              self.H.data_ptr(), s), "pnce_estimate")
-        check(L.pnce_scatter_rows(self.H.data_ptr(), self.klc, self.dst.data_ptr(),
-                                  self.cnt.data_ptr(), self.cap, s), "pnce_scatter_rows")
+        estimate_grouped(self.pilot, self.desc.data_ptr(), self.cap, self.cap, self.klc, eng.dtype,
+                         self.ws, stream=s)
 
     def run(self, eng: "GpuEngine", slot: int, reqs: list):
-        rows = 0
-        for r in reqs:
-            m = np.arange(r.M, dtype=np.int64)
-            self.src_np[rows:rows + r.M] = r.y_addr + m * (r.N * 8)
-            self.dst_np[rows:rows + r.M] = r.h_addr + m * (r.K * r.L * 8)
-            self.cnt_np[rows:rows + r.M] = r.K * r.L
-            rows += r.M
-        self.src_np[rows:] = 0
-        self.dst_np[rows:] = 0
-        self.cnt_np[rows:] = 0
+        n = len(reqs)
+        self.d_ptr[:n, 0] = [r.y_addr for r in reqs]
+        self.d_ptr[:n, 1] = [r.h_addr for r in reqs]
+        self.d_int[:n, 4] = [r.M for r in reqs]
+        self.d_int[:n, 5] = [r.K for r in reqs]
+        self.d_int[:n, 6] = [r.L for r in reqs]
+        self.d_int[:n, 7] = np.cumsum([0] + [r.M for r in reqs[:-1]])
+        self.d_int[n:, 4] = 0                              # empty slots
         stream = eng.streams[slot]
         with torch.cuda.stream(stream):
             if self.graph is not None:
