@@ -142,8 +142,9 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
 #pragma unroll
                         for (int i = 0; i < RA; ++i) {
                             const float yx = h ? yy[i].z : yy[i].x, yi = h ? yy[i].w : yy[i].y;
-                            acc[i][r].x = fmaf(pv, yx, acc[i][r].x);
-                            acc[i][r].y = fmaf(pv, yi, acc[i][r].y);
+                            // both parts in one packed FMA (each part rounded as fmaf)
+                            acc[i][r] = __ffma2_rn(make_float2(pv, pv), make_float2(yx, yi),
+                                                   acc[i][r]);
                         }
                     }
                 }
