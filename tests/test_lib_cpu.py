@@ -77,16 +77,29 @@ def test_null_arguments_rejected_without_device(lib):
                              None) == 1
 
 
-def test_missing_library_fails_loudly(tmp_path):
+def test_missing_library_fails_loudly():
     # no CPU or PyTorch fallback: without the built library the binding refuses to run
     from paper_2206_05506_gb300 import _lib
     saved = _lib._lib
     try:
         _lib._lib = None
         with pytest.raises(RuntimeError, match="libpnce.so not found"):
-            _lib.load(str(tmp_path / "libpnce.so"))
+            _lib.load(os.path.join(ROOT, "no_such_directory", "libpnce.so"))
     finally:
         _lib._lib = saved
+
+
+def test_new_entry_points_validate_before_any_device_use(lib):
+    # grouped serving estimate and the transform yardstick reject bad arguments up front
+    assert lib.pnce_estimate_grouped(None, None, None, 1, 64, 32, 2, None, 0, None) == 1
+    assert lib.pnce_grouped_workspace_size(0, 127, 16, 2) == 0          # no rows
+    assert lib.pnce_grouped_workspace_size(64, 127, 128, 2) == 0        # kl_max > N
+    assert lib.pnce_grouped_workspace_size(64, 127, 16, 99) == 0        # unknown dtype
+    assert lib.pnce_grouped_workspace_size(64, 127, 16, 0) > 0
+    assert lib.pnce_fmt_create(None, None, 127, None) == 1
+    assert lib.pnce_fmt_destroy(None) == 1
+    assert lib.pnce_estimate_fmt(None, None, None, 1, 1, 127, 1, 1, None, None) == 1
+    assert lib.pnce_estimate_static(None, None, None, 1, 1, 127, 1, 1, 2, None, None) == 1
 
 
 def test_product_code_does_not_import_the_oracle():
