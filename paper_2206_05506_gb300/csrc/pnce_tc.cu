@@ -47,8 +47,10 @@ namespace {
 constexpr int THREADS = 256;
 constexpr int BM = 128;                   // accumulator rows (TMEM lanes) per tile
 constexpr int STAGES = 8;                 // maximum pipeline depth
-constexpr int MIN_RES_STAGES = 4;         // fewest stages worth keeping the pilot resident
-constexpr int A_STAGE = BM * 128;         // 16 KB
+constexpr int MAX_KPS = 2;                // K blocks per pipeline stage (TMA boxes, 4 MMAs each):
+                                          // two halve the issuing thread's per-stage work per
+                                          // MMA, when shared memory leaves room for 3 stages
+constexpr int A_BOX = BM * 128;           // one TMA box: 128 rows x 128 B = 16 KB
 constexpr int ACC_COLS = 256;
 constexpr int TMEM_COLS = 512;
 constexpr int MAX_BN = 256;
@@ -61,7 +63,10 @@ struct TcParams {
     int BN;                 // lags per tile (multiple of 32, <= 256)
     int num_jt;             // lag blocks
     long long num_tiles;
-    int num_kb;             // pipeline stages per tile (K blocks)
+    int num_kb;             // K blocks of 128-byte rows per tile
+    int kps;                // K blocks per stage (1 or 2)
+    int a_stage;            // operand bytes per stage: kps * A_BOX
+    int num_st;             // pipeline stages per tile: ceil(num_kb / kps)
     int stages;             // pipeline depth (<= STAGES)
     int b_region;           // bytes of the pilot operand region
     int res_rows;           // resident pilot: 16-byte rows to generate (0 otherwise)
@@ -93,12 +98,12 @@ template <> struct TcFmt<PNCE_TF32> {
 };
 
 template <int DT>
-constexpr int ncm(int bn) {   // core matrices of one stage's pilot operand
-    using F = TcFmt<DT>;
-    return (bn / 8 - 1) * F::QS + (F::BK / F::EPR - 1) * F::TS + 1;
+__host__ __device__ constexpr int ncm(int bn, int kps) {   // core matrices of one stage's pilot
+    using F = TcFmt<DT>;                                   // operand (kps K blocks)
+    return (bn / 8 - 1) * F::QS + (kps * F::BK / F::EPR - 1) * F::TS + 1;
 }
 template <int DT>
-constexpr int b_stage_bytes() { return (ncm<DT>(MAX_BN) * 128 + 1023) / 1024 * 1024; }
+constexpr int b_stage_bytes() { return (ncm<DT>(MAX_BN, MAX_KPS) * 128 + 1023) / 1024 * 1024; }
 
 struct Ctl {
     unsigned long long full_a[STAGES];
@@ -394,7 +399,7 @@ __device__ __forceinline__ void gen_pilot_rows(unsigned char* dst, const uint32_
 
 // ------------------------------------------------------------------- the kernel
 
-template <int DT, bool RES>
+template <int DT, bool RES, int KPS>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
                const float* __restrict__ row_scale, float2* __restrict__ H, const TcParams prm) {
@@ -409,11 +414,13 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int nst = prm.stages;
     unsigned char* sA = base;
-    unsigned char* sB = sA + nst * A_STAGE;
+    unsigned char* sB = sA + nst * prm.a_stage;
     Ctl* ctl = reinterpret_cast<Ctl*>(sB + prm.b_region);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int BN = prm.BN, num_jt = prm.num_jt, num_kb = prm.num_kb;
+    const int BN = prm.BN, num_jt = prm.num_jt, num_st = prm.num_st;
+    constexpr int kps = KPS;                    // K blocks per stage (prm.kps)
+    constexpr int a_stage = KPS * A_BOX;        // prm.a_stage
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < nst; ++s) {
@@ -462,13 +469,17 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
             bool ok = true;
             for (long long t = blockIdx.x; t < prm.num_tiles && ok; t += gridDim.x) {
                 const int y = (int)(t / num_jt) * BM;
-                for (int kb = 0; kb < num_kb; ++kb) {
+                for (int st = 0; st < num_st; ++st) {
                     if (!wait_bar(&ctl->empty[stage], phase ^ 1u, ctl, prm, true)) {
                         ok = false;
                         break;
                     }
-                    mbar_arrive_tx(&ctl->full_a[stage], A_STAGE);
-                    tma_load_2d(sA + stage * A_STAGE, &tmap, kb * F::BK, y, &ctl->full_a[stage]);
+                    mbar_arrive_tx(&ctl->full_a[stage], a_stage);
+                    // boxes past the last K block read the fill value (zeros)
+#pragma unroll
+                    for (int h = 0; h < KPS; ++h)
+                        tma_load_2d(sA + stage * a_stage + h * A_BOX, &tmap,
+                                    (kps * st + h) * F::BK, y, &ctl->full_a[stage]);
                     ++issued;
                     if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
                 }
@@ -480,23 +491,23 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
         }
     } else if (warp == 1 && !RES) {
         // ---------------------------------------------------- pilot operand generator
-        const int rows = ncm<DT>(BN) * 8;
+        const int rows = ncm<DT>(BN, kps) * 8;
         uint32_t stage = 0, phase = 0;
         bool ok = true;
         for (long long t = blockIdx.x; t < prm.num_tiles && ok; t += gridDim.x) {
             long long j0;
             int col0, valid;
             pnce::lag_tile(prm.lags, BN, t % num_jt, j0, col0, valid);
-            for (int kb = 0; kb < num_kb; ++kb) {
+            for (int st = 0; st < num_st; ++st) {
                 int got = 1;
                 if (lane == 0) got = wait_bar(&ctl->empty[stage], phase ^ 1u, ctl, prm, true);
                 got = __shfl_sync(0xffffffffu, got, 0);
                 if (!got) { ok = false; break; }
-                const long long s_start = (long long)kb * F::BK - j0 - BN + 1;
+                const long long s_start = (long long)kps * st * F::BK - j0 - BN + 1;
                 gen_pilot_rows<DT>(sB + stage * BSTAGE, ext, prm.N, s_start, rows, lane, 32);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
-                const bool drop = prm.drop_first_arrive && t == blockIdx.x && kb == 0;
+                const bool drop = prm.drop_first_arrive && t == blockIdx.x && st == 0;
                 if (lane == 0 && !drop) mbar_arrive(&ctl->full_b[stage]);
                 if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
             }
@@ -519,21 +530,27 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                 if (!wait_bar(&ctl->tempty[acc], acc_phase ^ 1u, ctl, prm, true)) break;
                 fence_after();
                 const uint32_t d = tmem + acc * ACC_COLS;
-                for (int kb = 0; kb < num_kb; ++kb) {
+                for (int st = 0; st < num_st; ++st) {
                     if (!wait_bar(&ctl->full_a[stage], phase, ctl, prm, true) ||
                         (!RES && !wait_bar(&ctl->full_b[stage], phase, ctl, prm, true))) {
                         ok = false;
                         break;
                     }
                     fence_after();
-                    const uint64_t ad = adesc0 + (uint64_t)((stage * (uint32_t)A_STAGE) >> 4);
-                    // resident: K block kb starts BK/EPR core matrices (times TS) further on
+                    const uint64_t ad = adesc0 + (uint64_t)((stage * (uint32_t)a_stage) >> 4);
+                    // resident: K block kb starts BK/EPR core matrices (times TS) further on;
+                    // a stage's second K block is one such step after its first
                     const uint64_t bd =
-                        bdesc0 + (uint64_t)(RES ? (8u * F::TS * (uint32_t)(kb * (F::BK / F::EPR)))
+                        bdesc0 + (uint64_t)(RES ? (8u * F::TS * (uint32_t)(kps * st * (F::BK / F::EPR)))
                                                 : ((stage * (uint32_t)BSTAGE) >> 4));
 #pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ++ks)
-                        umma<DT>(d, ad + 2u * ks, bd + (KSTEP_B >> 4) * ks, idesc, (kb | ks) != 0);
+                    for (int h = 0; h < KPS; ++h)
+#pragma unroll
+                        for (int ks = 0; ks < KSTEPS; ++ks)
+                            umma<DT>(d, ad + (uint64_t)(h * (A_BOX >> 4)) + 2u * ks,
+                                     bd + (uint64_t)(h * 8 * F::TS * (F::BK / F::EPR)) +
+                                         (KSTEP_B >> 4) * ks,
+                                     idesc, (st | h | ks) != 0);
                     umma_commit(&ctl->empty[stage]);
                     last_bar = &ctl->empty[stage];
                     last_par = phase;
@@ -683,7 +700,7 @@ __device__ __forceinline__ void umma_pair(uint32_t tmem_d, uint64_t a, uint64_t 
     }
 }
 
-template <int DT>
+template <int DT, int KPS>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
                const float* __restrict__ row_scale, float2* __restrict__ H, const TcParams prm) {
@@ -697,12 +714,14 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int nst = prm.stages;
     unsigned char* sA = base;
-    unsigned char* sB = sA + nst * A_STAGE;
+    unsigned char* sB = sA + nst * prm.a_stage;
     PairCtl* ctl = reinterpret_cast<PairCtl*>(sB + prm.b_region);
     Ctl* wctl = reinterpret_cast<Ctl*>(ctl);    // abort flag shared with wait_bar
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int BN = prm.BN, num_jt = prm.num_jt, num_kb = prm.num_kb;
+    const int BN = prm.BN, num_jt = prm.num_jt, num_st = prm.num_st;
+    constexpr int kps = KPS;                    // K blocks per stage (prm.kps)
+    constexpr int a_stage = KPS * A_BOX;        // prm.a_stage
     const uint32_t rank = cluster_rank();
     const long long pair = cluster_id(), npairs = cluster_count();
 
@@ -759,14 +778,17 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
             bool ok = true;
             for (long long t = pair; t < prm.num_tiles && ok; t += npairs) {
                 const int y = (int)(2 * (t / num_jt) + rank) * BM;
-                for (int kb = 0; kb < num_kb; ++kb) {
+                for (int st = 0; st < num_st; ++st) {
                     if (!wait_bar(&ctl->empty[stage], phase ^ 1u, wctl, prm, true)) {
                         ok = false;
                         break;
                     }
-                    if (rank == 0) mbar_arrive_tx(&ctl->full_a[stage], 2 * A_STAGE);
-                    tma_load_2d_pair(sA + stage * A_STAGE, &tmap, kb * F::BK, y,
-                                     full0 + stage * (uint32_t)sizeof(unsigned long long));
+                    if (rank == 0) mbar_arrive_tx(&ctl->full_a[stage], 2 * a_stage);
+#pragma unroll
+                    for (int h = 0; h < KPS; ++h)
+                        tma_load_2d_pair(sA + stage * a_stage + h * A_BOX, &tmap,
+                                         (kps * st + h) * F::BK, y,
+                                         full0 + stage * (uint32_t)sizeof(unsigned long long));
                     ++issued;
                     if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
                 }
@@ -795,19 +817,23 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                 if (!wait_bar<true>(&ctl->tempty[acc], acc_phase ^ 1u, wctl, prm, true)) break;
                 fence_after();
                 const uint32_t d = tmem + acc * ACC_COLS;
-                for (int kb = 0; kb < num_kb; ++kb) {
+                for (int st = 0; st < num_st; ++st) {
                     if (!wait_bar<true>(&ctl->full_a[stage], phase, wctl, prm, true)) {
                         ok = false;
                         break;
                     }
                     fence_after();
-                    const uint64_t ad = adesc0 + (uint64_t)((stage * (uint32_t)A_STAGE) >> 4);
+                    const uint64_t ad = adesc0 + (uint64_t)((stage * (uint32_t)a_stage) >> 4);
                     const uint64_t bd =
-                        bdesc0 + (uint64_t)(8u * F::TS * (uint32_t)(kb * (F::BK / F::EPR)));
+                        bdesc0 + (uint64_t)(8u * F::TS * (uint32_t)(kps * st * (F::BK / F::EPR)));
 #pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ++ks)
-                        umma_pair<DT>(d, ad + 2u * ks, bd + (KSTEP_B >> 4) * ks, idesc,
-                                      (kb | ks) != 0);
+                    for (int h = 0; h < KPS; ++h)
+#pragma unroll
+                        for (int ks = 0; ks < KSTEPS; ++ks)
+                            umma_pair<DT>(d, ad + (uint64_t)(h * (A_BOX >> 4)) + 2u * ks,
+                                          bd + (uint64_t)(h * 8 * F::TS * (F::BK / F::EPR)) +
+                                              (KSTEP_B >> 4) * ks,
+                                          idesc, (st | h | ks) != 0);
                     umma_commit_pair(&ctl->empty[stage]);
                     last_bar = &ctl->empty[stage];
                     last_par = phase;
@@ -926,41 +952,56 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     prm.num_kb = (N + F::BK - 1) / F::BK;
     prm.wait_limit_ns = wait_limit_ns();
     prm.err = h->status_dev;
-    // a tile's products take ~num_kb * 4 MMAs of BN/2 cycles (M = 128, any operand type);
-    // the epilogue's chunks are spread over EPI_SPREAD of that
-    {
-        const long long nch = (prm.BN + 63) / 64;
-        const long long tile_cycles = (long long)prm.num_kb * 2LL * prm.BN;
-        prm.epi_spacing = nch > 1 ? (long long)(EPI_SPREAD * (double)tile_cycles) / nch : 0;
-    }
 
     long long grid = h->num_sms;
     if (grid >= prm.num_jt) grid = grid / prm.num_jt * prm.num_jt;
     if (grid > prm.num_tiles) grid = prm.num_tiles;
     if (grid < 1) return PNCE_OK;
 
-    // resident pilot operand when every CTA keeps one lag block and the list fits beside
-    // at least MIN_RES_STAGES pipeline stages
+    // Pipeline shape.  Resident pilot operand when every CTA keeps one lag block and the
+    // list for all K blocks fits beside the stages: two K blocks per stage when that still
+    // leaves 3 stages (32 KB each), else one K block per stage with at least 4 (16 KB).
+    // Otherwise the per-stage pilot generator, two K blocks per stage.
     const long long avail = (long long)h->max_smem_optin - (long long)smem_fixed();
-    const long long res_cm = (long long)(prm.BN / 8 - 1) * F::QS +
-                             ((long long)prm.num_kb * (F::BK / F::EPR) - 1) * F::TS + 1;
-    const long long res_bytes = (res_cm * 128 + 1023) / 1024 * 1024;
+    auto res_cm_for = [&](int bn, int kps) {   // core matrices of the resident list
+        const long long nst = (prm.num_kb + kps - 1) / kps;
+        return (long long)(bn / 8 - 1) * F::QS + (nst * kps * (F::BK / F::EPR) - 1) * F::TS + 1;
+    };
+    auto kbytes = [](long long cm) { return (cm * 128 + 1023) / 1024 * 1024; };
     // PNCE_TC_STAGED_PILOT=1 forces the per-stage pilot path (used to test both paths);
     // PNCE_TC_TEST_DROP_ARRIVE=1 (staged path only) withholds one arrive so that the test of
     // the bounded waits sees PNCE_ETIMEOUT latched and the context still usable
     const char* force = getenv("PNCE_TC_STAGED_PILOT");
     const char* drop = getenv("PNCE_TC_TEST_DROP_ARRIVE");
     prm.drop_first_arrive = (drop && drop[0] == '1') ? 1 : 0;
-    const bool res = !(force && force[0] == '1') && (grid % prm.num_jt == 0) &&
-                     (avail - res_bytes) / A_STAGE >= MIN_RES_STAGES;
-    if (res) {
-        prm.stages = (int)std::min<long long>(STAGES, (avail - res_bytes) / A_STAGE);
-        prm.b_region = (int)res_bytes;
-        prm.res_rows = (int)(res_cm * 8);
-    } else {
-        prm.stages = STAGES;
-        prm.b_region = STAGES * b_stage_bytes<DT>();
+    const bool may_res = !(force && force[0] == '1') && (grid % prm.num_jt == 0);
+    bool res = false;
+    for (int kps = MAX_KPS; kps >= 1 && may_res && !res; --kps) {
+        const long long cm = res_cm_for(prm.BN, kps);
+        const long long st = (avail - kbytes(cm)) / (kps * A_BOX);
+        if (st >= (kps == 2 ? 3 : 4)) {
+            res = true;
+            prm.kps = kps;
+            prm.stages = (int)std::min<long long>(STAGES, st);
+            prm.b_region = (int)kbytes(cm);
+            prm.res_rows = (int)(cm * 8);
+        }
+    }
+    if (!res) {
+        prm.kps = MAX_KPS;
+        prm.stages = (int)std::min<long long>(
+            STAGES, avail / (MAX_KPS * A_BOX + b_stage_bytes<DT>()));
+        prm.b_region = prm.stages * b_stage_bytes<DT>();
         prm.res_rows = 0;
+    }
+    prm.a_stage = prm.kps * A_BOX;
+    prm.num_st = (prm.num_kb + prm.kps - 1) / prm.kps;
+    // a tile's products take ~num_kb * 4 MMAs of BN/2 cycles (M = 128, any operand type);
+    // the epilogue's chunks are spread over EPI_SPREAD of that
+    {
+        const long long nch = (prm.BN + 63) / 64;
+        const long long tile_cycles = (long long)prm.num_st * prm.kps * 2LL * prm.BN;
+        prm.epi_spacing = nch > 1 ? (long long)(EPI_SPREAD * (double)tile_cycles) / nch : 0;
     }
     // 2-SM variant (opt-in while it is being evaluated): CTA pairs, each CTA with half of a
     // BN-lag tile's pilot list; pairs stay on one lag block, so their count is a multiple
@@ -972,19 +1013,26 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
         long long pairs = h->num_sms / 2;
         if (pairs >= prm.num_jt) pairs = pairs / prm.num_jt * prm.num_jt;
         if (pairs > ptiles) pairs = ptiles;
-        const long long res_cm2 = (long long)(prm.BN / 16 - 1) * F::QS +
-                                  ((long long)prm.num_kb * (F::BK / F::EPR) - 1) * F::TS + 1;
-        const long long res_bytes2 = (res_cm2 * 128 + 1023) / 1024 * 1024;
-        if (pairs >= 1 && pairs % prm.num_jt == 0 && prm.BN % 32 == 0 &&
-            (avail - res_bytes2) / A_STAGE >= MIN_RES_STAGES) {
-            TcParams pp = prm;
+        TcParams pp = prm;
+        bool ok2 = false;
+        for (int kps = MAX_KPS; kps >= 1 && !ok2; --kps) {
+            const long long cm = res_cm_for(prm.BN / 2, kps);
+            const long long st = (avail - kbytes(cm)) / (kps * A_BOX);
+            if (st >= (kps == 2 ? 3 : 4)) {
+                ok2 = true;
+                pp.kps = kps;
+                pp.a_stage = kps * A_BOX;
+                pp.num_st = (prm.num_kb + kps - 1) / kps;
+                pp.stages = (int)std::min<long long>(STAGES, st);
+                pp.b_region = (int)kbytes(cm);
+                pp.res_rows = (int)(cm * 8);
+            }
+        }
+        if (pairs >= 1 && pairs % prm.num_jt == 0 && prm.BN % 32 == 0 && ok2) {
             pp.num_tiles = ptiles;
-            pp.stages = (int)std::min<long long>(STAGES, (avail - res_bytes2) / A_STAGE);
-            pp.b_region = (int)res_bytes2;
-            pp.res_rows = (int)(res_cm2 * 8);
-            const size_t smem2 = smem_fixed() + (size_t)pp.stages * A_STAGE + pp.b_region;
-            if (cudaFuncSetAttribute(tc_pair_kernel<DT>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+            const size_t smem2 = smem_fixed() + (size_t)pp.stages * pp.a_stage + pp.b_region;
+            auto pk = pp.kps == 2 ? tc_pair_kernel<DT, 2> : tc_pair_kernel<DT, 1>;
+            if (cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)smem2) != cudaSuccess)
                 return PNCE_ECUDA;
             cudaLaunchConfig_t cfg = {};
@@ -1000,14 +1048,16 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             const cudaError_t le =
-                cudaLaunchKernelEx(&cfg, tc_pair_kernel<DT>, map, pilot->ext_bits_dev, factors, H, pp);
+                cudaLaunchKernelEx(&cfg, pk, map, pilot->ext_bits_dev, factors, H, pp);
             return le == cudaSuccess ? PNCE_OK : PNCE_ECUDA;
         }
     }
 
-    const size_t smem = smem_fixed() + (size_t)prm.stages * A_STAGE + prm.b_region;
+    const size_t smem = smem_fixed() + (size_t)prm.stages * prm.a_stage + prm.b_region;
     if ((long long)smem > h->max_smem_optin) return PNCE_EUNSUPPORTED;
-    auto kern = res ? tc_corr_kernel<DT, true> : tc_corr_kernel<DT, false>;
+    // the staged path always takes two K blocks per stage
+    auto kern = !res ? tc_corr_kernel<DT, false, 2>
+                     : (prm.kps == 2 ? tc_corr_kernel<DT, true, 2> : tc_corr_kernel<DT, true, 1>);
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return PNCE_ECUDA;
