@@ -405,7 +405,7 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
                const float* __restrict__ row_scale, float2* __restrict__ H, const TcParams prm) {
     using F = TcFmt<DT>;
     constexpr int BSTAGE = b_stage_bytes<DT>();
-    constexpr int KSTEPS = 4;                  // MMAs per stage: 128 B of K, 32 B each
+    constexpr int KSTEPS = 4;                  // MMAs per K block: 128 B of K, 32 B each
     constexpr uint32_t LBO = 128u * F::TS, SBO = 128u * F::QS;
     constexpr uint32_t KSTEP_B = 2u * 128u * F::TS;       // B bytes per MMA K step
 
