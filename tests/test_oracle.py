@@ -328,7 +328,7 @@ def test_scale_exponents():
     assert np.all(peak[:3] >= 128) and np.all(peak[:3] < 256)
 
 
-def test_quantized_estimate_within_north_star_tolerances():
+def test_quantized_estimate_within_stated_tolerances():
     bits, _, Y = _small_case(10, 16, 4, 64, 2, seed=9, snr=10.0)
     ref = O.estimate(Y, bits, 4, 64)
     for fmt, tol in (("fp16", 2e-3), ("bf16", 2e-3), ("e4m3", 3e-2), ("tf32", 1e-6)):
