@@ -45,7 +45,7 @@ extern "C" {
 typedef enum {
     PNCE_OK = 0,
     PNCE_EINVAL = 1,        /* bad argument: shape, null or misaligned pointer, small workspace */
-    PNCE_EUNSUPPORTED = 2,  /* valid request this build or device cannot serve */
+    PNCE_EUNSUPPORTED = 2,  /* valid request the library or device cannot serve */
     PNCE_ENOMEM = 3,        /* a create function could not allocate */
     PNCE_ECUDA = 4,         /* a CUDA runtime call failed */
     PNCE_ETIMEOUT = 5,      /* a device-side bounded wait ran out (latched, see pnce_get_status) */
