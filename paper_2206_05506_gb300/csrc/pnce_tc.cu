@@ -4,11 +4,12 @@
 //   C[r][j] = sum_n A[r][n] * B[n][j],  B[n][j] = p[(n - j) mod N]  (the circulant, Eq. 2)
 //
 // A: the quantised received block in 8-antenna groups of 16 rows (the 8 real parts, then
-//    the 8 imaginary parts), staged 128 rows x 128 B per pipeline stage by TMA with the
-//    128-byte swizzle.
+//    the 8 imaginary parts), staged by TMA with the 128-byte swizzle in boxes of 128 rows
+//    x 128 B (one K block), one or two boxes per pipeline stage.
 // B: never stored in HBM.  The lag order inside a tile is reversed (tile column i holds
 //    lag j0 + BN - 1 - i, j0 the tile's first lag: k*L-contiguous tiles, or per-transmitter
-//    tiles when the transmitters' cyclic shifts are spread out), which turns the Toeplitz tile into a Hankel one: the value at
+//    tiles when the transmitters' cyclic shifts are spread out), which turns the Toeplitz
+//    tile into a Hankel one: the value at
 //    (column 8q + r, sample n0 + EPR*t + c) is p[(s + G*(QS*q + TS*t) + r + c) mod N].
 //    Every 8-row x 16-byte core matrix of the canonical no-swizzle K-major layout is then
 //    one of a short list indexed by D = QS*q + TS*t, so the pilot operand of a stage is
@@ -17,7 +18,7 @@
 //    lag block only shift along that list, so when it fits, the whole list for every K
 //    block of the CTA's lag block (N/8 + BN/8 core matrices for 16-bit types, ~70 KB at
 //    N = 4095) is generated once at kernel start and stays resident ("resident pilot");
-//    otherwise one warp regenerates each stage's list (<= 70 core matrices, <= 9 KB).
+//    otherwise one warp regenerates each stage's list (<= 78 core matrices, <= 10 KB).
 // Epilogue: tcgen05.ld in the 16x256b shape hands each thread the real and imaginary
 //    accumulators of one antenna for two adjacent columns (the group layout puts the two
 //    parts 8 TMEM lanes apart), so after the per-antenna factor 2^-s_a / N each thread
