@@ -57,8 +57,10 @@ class Context:
     """A pnce_handle bound to one CUDA device (latched device status word)."""
 
     def __init__(self, device=None):
-        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
-                                   else torch.device(device).index or 0)
+        d = None if device is None else torch.device("cuda", device) if isinstance(device, int) \
+            else torch.device(device)
+        idx = d.index if d is not None and d.index is not None else torch.cuda.current_device()
+        self.device = torch.device("cuda", idx)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
             check(lib().pnce_create(C.byref(h)), "pnce_create")
