@@ -171,6 +171,81 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
     }
 }
 
+// Few lags (K*L <= 32, lags contiguous): the block tile above would leave most lanes idle,
+// and at ~2 K*L flops per 8-byte sample the work is close to the HBM roofline.  One warp
+// per received row: lane l takes samples l, l+32, ... (coalesced 8-byte loads, read once)
+// and reads the pilot bits b[n-K*L+1 .. n] as one window of the wrapped bit table.  With
+// p = 1 - 2b, sum_n y[n] p[n-j] = S - 2 B_j, S = sum_n y[n] and B_j the sum of the samples
+// whose bit b[n-j] is set, so each lag costs one bit test and one predicated packed add.
+// A butterfly reduction over the warp (the same sum on every lane) ends the row and lane
+// j stores lag j.
+template <int KLM>
+__global__ void __launch_bounds__(256)
+simt_few_lags_kernel(const uint32_t* __restrict__ ext, const float2* __restrict__ Y,
+                     long long y_stride, long long A, int N, int KL, int ldH, float invN,
+                     float2* __restrict__ H) {
+    const int lane = threadIdx.x & 31;
+    const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long a = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; a < A;
+         a += nwarps) {
+        const float2* y = Y + a * y_stride;
+        float2 acc[KLM];                       // B_j
+        float2 all = make_float2(0.f, 0.f);     // S
+#pragma unroll
+        for (int j = 0; j < KLM; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int n = lane; n < N; n += 32) {
+            const float2 v = __ldcs(y + n);
+            // bits of samples n-KL+1 .. n (mod N): bit i of w is pilot bit q + i, and lag
+            // j meets bit n - j, i.e. bit KL-1-j of w; the table wraps past N, so q < N
+            // keeps the window inside it
+            int q = n - (KL - 1);
+            if (q < 0) q += N;
+            const uint32_t lo = __ldg(ext + (q >> 5)), hi = __ldg(ext + (q >> 5) + 1);
+            const uint32_t w = (uint32_t)((((uint64_t)hi << 32) | lo) >> (q & 31));
+            all = __fadd2_rn(all, v);
+            // lag j: bit KL-1-j of w; reversed so that the bit test is by a constant
+            const uint32_t wr = __brev(w) >> (32 - KL);     // bit j of wr = bit KL-1-j of w
+#pragma unroll
+            for (int j = 0; j < KLM; ++j)
+                if ((wr >> j) & 1u) acc[j] = __fadd2_rn(acc[j], v);
+        }
+        float2 mine = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < KLM; ++j) {
+            if (j < KL) {                                  // uniform over the warp
+                float re = all.x - 2.f * acc[j].x, im = all.y - 2.f * acc[j].y;
+#pragma unroll
+                for (int o = 16; o; o >>= 1) {
+                    re += __shfl_xor_sync(0xffffffffu, re, o);
+                    im += __shfl_xor_sync(0xffffffffu, im, o);
+                }
+                if (lane == j) mine = make_float2(re * invN, im * invN);
+            }
+        }
+        if (lane < KL) H[a * ldH + lane] = mine;
+    }
+}
+
+template <int KLM>
+cudaError_t launch_few(const uint32_t* ext, const float2* Y, long long y_stride, long long A,
+                       int N, int KL, int ldH, float2* H, cudaStream_t s) {
+    long long blocks = (A + 7) / 8;                 // 8 rows (warps) per block
+    if (blocks > 8LL * 1024 * 152) blocks = 8LL * 1024 * 152;
+    simt_few_lags_kernel<KLM><<<(unsigned)blocks, 256, 0, s>>>(
+        ext, Y, y_stride, A, N, KL, ldH, (float)(1.0 / (double)N), H);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_few_lags(const uint32_t* ext, const float2* Y, long long y_stride,
+                            long long A, int N, int KL, int ldH, float2* H, cudaStream_t s) {
+    if (A <= 0) return cudaSuccess;
+    if (KL <= 8) return launch_few<8>(ext, Y, y_stride, A, N, KL, ldH, H, s);
+    if (KL <= 16) return launch_few<16>(ext, Y, y_stride, A, N, KL, ldH, H, s);
+    return launch_few<32>(ext, Y, y_stride, A, N, KL, ldH, H, s);
+}
+
+constexpr int FEW_LAGS = 32;    // largest K*L the few-lags kernel takes
+
 template <int MODE>
 cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, long long y_stride,
                    long long A, int N, const pnce::LagMap& lags, int nmod, float2* H,
@@ -197,6 +272,7 @@ namespace pnce {
 
 cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s) {
+    if (KL <= FEW_LAGS) return launch_few_lags(pilot->ext_bits_dev, Y, N, A, N, KL, KL, H, s);
     return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Y, N, A, N, lagmap_contiguous(KL), N,
                             H, s);
 }
@@ -204,6 +280,8 @@ cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long
 cudaError_t launch_simt_bits_ex(const pnce_pilot* pilot, const float2* Y, long long y_stride,
                                 long long A, int N, const LagMap& lags, float2* H,
                                 cudaStream_t s) {
+    if (lags.mode == 0 && lags.ldH <= FEW_LAGS)
+        return launch_few_lags(pilot->ext_bits_dev, Y, y_stride, A, N, lags.ldH, lags.ldH, H, s);
     return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Y, y_stride, A, N, lags, N, H, s);
 }
 

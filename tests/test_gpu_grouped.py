@@ -67,7 +67,13 @@ def test_grouped_equals_per_request(pk, dtype, host):
     assert pk.get_status(dev) == 0
     for M, K, L, Y, H in reqs:
         ref = pk.estimate(Y.cuda().view(1, M, N), pilot, K, L, dtype=dtype).reshape(M, K * L)
-        assert torch.equal(H.cpu(), ref.cpu())
+        if dtype == "fp32" and K * L <= 32:
+            # alone, a request of few lags takes the few-lags FP32 kernel, whose sums run in
+            # another order than the batch's tiled kernel: equal to FP32 rounding
+            a, b = H.cpu().numpy(), ref.cpu().numpy()
+            assert np.sum(np.abs(a - b) ** 2) <= 1e-12 * np.sum(np.abs(b) ** 2)
+        else:
+            assert torch.equal(H.cpu(), ref.cpu())
 
 
 def test_grouped_invalid_descriptor_is_skipped(pk):
