@@ -193,6 +193,8 @@ simt_few_lags_kernel(const uint32_t* __restrict__ ext, const float2* __restrict_
         float2 all = make_float2(0.f, 0.f);     // S
 #pragma unroll
         for (int j = 0; j < KLM; ++j) acc[j] = make_float2(0.f, 0.f);
+        // several samples in flight per lane (the loads are the latency to hide)
+#pragma unroll (KLM >= 16 ? 4 : 2)
         for (int n = lane; n < N; n += 32) {
             const float2 v = __ldcs(y + n);
             // bits of samples n-KL+1 .. n (mod N): bit i of w is pilot bit q + i, and lag
