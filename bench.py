@@ -380,7 +380,7 @@ def main():
     ap.add_argument("--workload", default=C.PRECISION.name, choices=sorted(C.WORKLOADS))
     ap.add_argument("--dtype", default="fp16", choices=["fp32", "tf32", "fp16", "bf16", "e4m3"])
     ap.add_argument("--frames", type=int, default=None, help="override frames per step")
-    ap.add_argument("--e2e-steps", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ref-frames", type=int, default=8, help="frames per reference step")
     ap.add_argument("--serving-seconds", type=float, default=1.0,
