@@ -383,7 +383,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ref-frames", type=int, default=8, help="frames per reference step")
-    ap.add_argument("--serving-seconds", type=float, default=1.0,
+    ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the Poisson serving trace (0: skip)")
     ap.add_argument("--differentiation", type=int, default=1,
                     help="also time the relaxed-pilot forward + adjoint (1/0)")
