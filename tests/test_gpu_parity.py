@@ -165,7 +165,11 @@ def test_noise_free_recovery_closed_form(pk):
 def test_real_pilot_forward_and_adjoint(pk):
     dev = torch.device("cuda", 0)
     rng = np.random.default_rng(1)
-    for (F, M, N, K, L) in [(2, 3, 31, 2, 5), (3, 40, 1023, 8, 64), (1, 5, 300, 3, 100)]:
+    # shapes: N below a warp's width and the degenerate N = 2; several 128-lag chunks and
+    # 256-output tiles; more antennas than the dp grid's warps per tile (1500 at N = 511)
+    for (F, M, N, K, L) in [(2, 3, 31, 2, 5), (3, 40, 1023, 8, 64), (1, 5, 300, 3, 100),
+                            (1, 1, 7, 1, 7), (1, 2, 2, 1, 2), (3, 500, 511, 2, 128),
+                            (1, 40, 4095, 16, 128)]:
         Y = (rng.standard_normal((F, M, N)) + 1j * rng.standard_normal((F, M, N))).astype(np.complex64)
         p = np.tanh(rng.standard_normal(N)).astype(np.float32)
         G = (rng.standard_normal((F, M, K, L)) + 1j * rng.standard_normal((F, M, K, L))).astype(np.complex64)
