@@ -5,12 +5,15 @@
 // with p'[x] = p[-x mod N].  In general: out[a][o] = scale * sum_{k < Kred} in[a][k] *
 // pilot[(k - o) mod Nmod], o < Nout.
 //
-// Block tile: 32 antennas x 256 lags; thread tile: 4 antennas x 8 consecutive lags, so
-// each received sample read from shared memory feeds 64 FMAs.  Because a thread's lags
+// Block tile: up to 32 antennas x 256 lags (the rows are split into balanced groups so that
+// the grid fills whole waves); thread tile: 4 antennas x 8 consecutive lags, so each
+// received sample read from shared memory feeds 64 FMAs.  Because a thread's lags
 // are consecutive, the pilot values it needs at sample n+1 are those of sample n shifted
 // by one lag: a 15-entry register window slides along the pilot, one new shared load per
 // sample.  Received samples and the pilot window of each 128-sample chunk are staged in
 // shared memory, double buffered (cp.async for Y).
+#include <algorithm>
+
 #include "pnce_internal.h"
 
 namespace {
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(256, 2)
 simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ preal,
                  const float2* __restrict__ Y, long long y_stride, long long A,
                  int N /* reduction length */, const pnce::LagMap lags, int nmod, int num_jt,
-                 float invN, float2* __restrict__ H) {
+                 long long groups, float invN, float2* __restrict__ H) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
 
@@ -76,7 +79,10 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
     long long j0;            // first lag of this block's tile
     int col0, valid;         // its first output column and number of lags kept
     pnce::lag_tile(lags, TJ, bid % num_jt, j0, col0, valid);
-    const long long a0 = (bid / num_jt) * TA;
+    // antenna group g of a balanced partition of the A rows into `groups` (<= TA rows each)
+    const long long g = bid / num_jt, gbase = A / groups, grem = A % groups;
+    const long long a0 = g * gbase + (g < grem ? g : grem);
+    const int rows = (int)(gbase + (g < grem ? 1 : 0));
     const int nchunks = (N + NC - 1) / NC;
     // chunk-local pilot entry t holds p[(c*NC + t - (j0 + TJ - 1)) mod N]
     const long long eoff = j0 + TJ - 1;
@@ -86,7 +92,7 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
         for (int i = tid; i < TA * NC; i += 256) {
             const int aa = i / NC, nn = i % NC;
             const long long a = a0 + aa;
-            const bool ok = (a < A) && (n0 + nn < N);
+            const bool ok = (aa < rows) && (n0 + nn < N);
             const float2* src = ok ? (Y + a * y_stride + n0 + nn) : Y;
             cp_async8(&sm.y[buf][aa][nn], src, ok);
         }
@@ -116,6 +122,7 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
         const int buf = c & 1;
         if (c + 1 < nchunks) stage(c + 1, buf ^ 1);
 
+        if (warp * RA < rows) {                  // warps past the group's rows only stage
         const float* e = sm.e[buf];
         float w[15];
 #pragma unroll
@@ -154,14 +161,15 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
 #pragma unroll
             for (int i = 0; i < 8; ++i) w[7 + i] = nw[i];
         }
+        }
         cp_async_wait_all();
         __syncthreads();
     }
 
 #pragma unroll
     for (int i = 0; i < RA; ++i) {
+        if (warp * RA + i >= rows) continue;
         const long long a = a0 + warp * RA + i;
-        if (a >= A) continue;
         float2* hrow = H + a * lags.ldH + col0;
 #pragma unroll
         for (int r = 0; r < RJ; ++r) {
@@ -255,16 +263,34 @@ cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, lo
     const long long num_jt_ll = pnce::lag_tiles(lags, TJ);
     if (num_jt_ll > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int num_jt = (int)num_jt_ll;
-    const long long blocks = (long long)num_jt * ((A + TA - 1) / TA);
-    if (blocks <= 0) return cudaSuccess;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (A <= 0 || num_jt <= 0) return cudaSuccess;
     const size_t smem = sizeof(Smem);
     cudaError_t e = cudaFuncSetAttribute(simt_corr_kernel<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // Antenna groups: at least ceil(A / TA), raised so that the grid fills whole waves of the
+    // resident blocks (tiles of 2^k rows leave the last wave partly empty on 152 SMs).  The
+    // grouping changes no result: every output is summed over n in the same order.
+    long long groups = (A + TA - 1) / TA;
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_corr_kernel<MODE>, 256,
+                                                           smem)) != cudaSuccess)
+        return e;
+    if (sms > 0 && per_sm > 0) {
+        const long long slots = (long long)sms * per_sm;
+        const long long waves = (groups * num_jt + slots - 1) / slots;
+        const long long even = waves * slots / num_jt;
+        groups = std::min(A, std::max(groups, even));
+    }
+    const long long blocks = (long long)num_jt * groups;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const float invN = (float)(1.0 / (double)nmod);
     simt_corr_kernel<MODE><<<(unsigned)blocks, 256, smem, s>>>(bits, preal, Y, y_stride, A, N,
-                                                               lags, nmod, num_jt, invN, H);
+                                                               lags, nmod, num_jt, groups, invN,
+                                                               H);
     return cudaGetLastError();
 }
 
