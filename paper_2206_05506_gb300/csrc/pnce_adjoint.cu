@@ -36,11 +36,13 @@ struct DpShape {
     static constexpr int WN = R + 7;              // register window entries
     static constexpr int WLEN = JC + QT + 8;      // staged window entries (a lane reads up to
                                                   // R*31 + WN + 8*14 + 7 < WLEN)
-    static constexpr int WPAD = ((WLEN + WLEN / 8 + 1) + 1) & ~1;   // even: g 16-byte aligned
+    static constexpr int WPAD = ((WLEN + WLEN / R + 1) + 1) & ~1;   // even: g 16-byte aligned
 };
 
-// float2 entries padded by one per 8 so that lanes 8 entries apart hit distinct banks
-__device__ __forceinline__ int wpos(int t) { return t + (t >> 3); }
+// float2 entries padded by one per R, so that lanes R entries apart are R + 1 (odd) float2
+// apart and a half-warp's 8-byte loads hit 16 distinct bank pairs
+template <int R>
+__device__ __forceinline__ int wpos(int t) { return t + t / R; }
 
 template <int R>
 struct __align__(16) DpStage {
@@ -68,13 +70,13 @@ __device__ __forceinline__ void dp_stage(DpStage<R>& st, const float2* yrow, con
         for (int i = 0; i < (WLEN + 31) / 32; ++i) {
             const int t = lane + 32 * i;
             const int pos = p0 + t >= N ? p0 + t - N : p0 + t;
-            if (t < WLEN) cp_async8(&st.w[wpos(t)], yrow + pos, true);
+            if (t < WLEN) cp_async8(&st.w[wpos<R>(t)], yrow + pos, true);
         }
     } else {
         int pos = (p0 + lane) % N;
         for (int i = 0; i < (WLEN + 31) / 32; ++i) {
             const int t = lane + 32 * i;
-            if (t < WLEN) cp_async8(&st.w[wpos(t)], yrow + pos, true);
+            if (t < WLEN) cp_async8(&st.w[wpos<R>(t)], yrow + pos, true);
             pos = (pos + 32) % N;
         }
     }
@@ -133,13 +135,13 @@ dp_partial_kernel(const float2* __restrict__ G, const float2* __restrict__ Y, lo
         const int base = R * lane;
         float2 w[WN];
 #pragma unroll
-        for (int i = 0; i < WN; ++i) w[i] = st.w[wpos(base + i)];
+        for (int i = 0; i < WN; ++i) w[i] = st.w[wpos<R>(base + i)];
 #pragma unroll
         for (int s = 0; s < JC / 8; ++s) {
             float2 nw[8];
             if (s + 1 < JC / 8) {
 #pragma unroll
-                for (int i = 0; i < 8; ++i) nw[i] = st.w[wpos(base + 8 * s + WN + i)];
+                for (int i = 0; i < 8; ++i) nw[i] = st.w[wpos<R>(base + 8 * s + WN + i)];
             }
             const float4* g4 = reinterpret_cast<const float4*>(st.g + 8 * s);
 #pragma unroll
