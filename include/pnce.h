@@ -222,13 +222,16 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
 
 /*
  * Tracing.  While enabled, the estimate entry points (pnce_estimate, pnce_estimate_ex,
- * pnce_quantize, pnce_correlate_quantized, pnce_estimate_grouped, pnce_estimate_fmt) record
- * a CUDA event before and after every quantiser / correlation kernel they launch, on the
- * stream that kernel runs on (internal streams included), up to 8192 kernels.
+ * pnce_quantize, pnce_correlate_quantized, pnce_estimate_grouped, pnce_estimate_fmt,
+ * pnce_estimate_real_pilot, pnce_backward) record a CUDA event before and after every
+ * quantiser / correlation / adjoint launch, on the stream it runs on (internal streams
+ * included), up to 8192 launches.  Each such launch is also an NVTX range named
+ * "pnce.<kind>" (always on; a no-op unless a profiler is attached).
  * pnce_trace_enable creates the events on first use (allocates host and event resources,
  * not device memory) and clears the record; pnce_trace_read waits for the recorded kernels,
  * returns up to max_entries (kind, milliseconds) pairs -- kind 0 quantiser, 1 tensor-core
- * correlation, 2 FP32 SIMT correlation, 3 fast m-sequence transform -- in launch order, and
+ * correlation, 2 FP32 SIMT correlation, 3 fast m-sequence transform, 4 adjoint (dY and
+ * dp together) -- in launch order, and
  * clears the record.  Do not enable it while capturing a CUDA graph.
  */
 pnce_status pnce_trace_enable(pnce_handle* h, int on);

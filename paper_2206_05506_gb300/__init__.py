@@ -101,7 +101,7 @@ def trace_enable(on: bool = True, device=None):
     check(lib().pnce_trace_enable(ctx.handle, 1 if on else 0), "pnce_trace_enable")
 
 
-TRACE_KINDS = {0: "quantize", 1: "correlate", 2: "simt", 3: "fmt"}
+TRACE_KINDS = {0: "quantize", 1: "correlate", 2: "simt", 3: "fmt", 4: "adjoint"}
 
 
 def trace_read(device=None, max_entries: int = 8192):

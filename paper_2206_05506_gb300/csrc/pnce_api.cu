@@ -428,6 +428,7 @@ pnce_status pnce_estimate_real_pilot(pnce_handle* h, const float* p_dev, int pil
     if (!aligned16(Y_dev) || !aligned16(H_dev) || !aligned16(p_dev)) return PNCE_EINVAL;
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
+    pnce::TraceScope tr(h, static_cast<cudaStream_t>(stream), pnce::TRACE_SIMT);
     return from_cuda(pnce::launch_simt_real(p_dev, pilot_map == PNCE_PILOT_TANH,
                                             static_cast<const float2*>(Y_dev),
                                             (long long)F * M, N, K * L,
@@ -457,6 +458,7 @@ pnce_status pnce_backward(pnce_handle* h, const float* p_dev, int pilot_map, con
     }
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
+    pnce::TraceScope tr(h, static_cast<cudaStream_t>(stream), pnce::TRACE_ADJOINT);
     return from_cuda(pnce::launch_backward(
         p_dev, pilot_map == PNCE_PILOT_TANH, static_cast<const float2*>(Y_dev),
         static_cast<const float2*>(G_dev),

@@ -7,6 +7,8 @@
 
 #include <mutex>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pnce.h"
 
 // chunk slots of the host-buffer pipeline (pnce_estimate_host)
@@ -40,13 +42,26 @@ struct pnce_handle {
 
 namespace pnce {
 constexpr int kTraceMax = 8192;
-enum TraceKind { TRACE_QUANTIZE = 0, TRACE_CORRELATE = 1, TRACE_SIMT = 2, TRACE_FMT = 3 };
+enum TraceKind {
+    TRACE_QUANTIZE = 0,
+    TRACE_CORRELATE = 1,
+    TRACE_SIMT = 2,
+    TRACE_FMT = 3,
+    TRACE_ADJOINT = 4,
+};
+// NVTX range names (profilers can filter launches by them)
+inline const char* trace_name(int kind) {
+    static const char* const names[] = {"pnce.quantize", "pnce.correlate", "pnce.simt",
+                                        "pnce.fmt", "pnce.adjoint"};
+    return kind >= 0 && kind <= TRACE_ADJOINT ? names[kind] : "pnce";
+}
 // Records a start event before / an end event after one kernel launch when tracing is on.
 struct TraceScope {
     pnce_handle* h;
     cudaStream_t s;
     int slot;
     TraceScope(pnce_handle* h_, cudaStream_t s_, int kind) : h(h_), s(s_), slot(-1) {
+        nvtxRangePushA(trace_name(kind));     // a no-op unless a profiler is attached
         if (h && h->trace_on) {
             std::lock_guard<std::recursive_mutex> g(h->lock);
             if (h->trace_n < kTraceMax) {
@@ -58,6 +73,7 @@ struct TraceScope {
     }
     ~TraceScope() {
         if (slot >= 0) cudaEventRecord(h->trace_ev[2 * slot + 1], s);
+        nvtxRangePop();
     }
 };
 }  // namespace pnce

@@ -16,7 +16,10 @@ taps) whose received blocks sit in page-locked host memory.  The loop
   buffer, estimates (quantise + tensor-core correlation, or the FP32 SIMT path) and
   scatters each antenna's lags straight into its request's host result buffer;
 * polls the batches' events and stamps each request's completion; latency is completion
-  minus scheduled arrival.
+  minus scheduled arrival;
+* if the engine raises while launching or polling a batch, that batch's requests are
+  recorded as failed (with the error), their memory and stream slot are released, and the
+  loop goes on with the rest.
 
 Pilot tables and the per-shape buffers stay resident on the device.  Each request's result
 depends only on its own antenna rows (per-antenna scales, fixed reduction order), so it is
@@ -60,6 +63,7 @@ class Request:
     t_launch: float = -1.0
     t_done: float = -1.0
     batch: int = -1
+    error: str = ""
 
 
 @dataclass
@@ -84,6 +88,7 @@ class Server:
         self.free_slots = list(range(engine.slots))[::-1]
         self.busy: list[_Busy] = []
         self.done: list[Request] = []
+        self.failed: list[Request] = []
         self.batches = 0
         self.batch_rows: list[int] = []
 
@@ -104,11 +109,24 @@ class Server:
             key = (r.N, kl_class(r.K * r.L, r.N))
             self.buckets.setdefault(key, collections.deque()).append(r)
 
+    def _fail(self, reqs: list, slot: int, now: float, exc: Exception):
+        for r in reqs:
+            r.t_done = now
+            r.error = f"{type(exc).__name__}: {exc}"
+            self.inflight_bytes -= r.nbytes
+            self.failed.append(r)
+        self.free_slots.append(slot)
+
     # -- completions
     def _complete(self, now: float):
         still = []
         for b in self.busy:
-            if self.engine.done(b.token):
+            try:
+                finished = self.engine.done(b.token)
+            except Exception as exc:                   # noqa: BLE001 -- reported per request
+                self._fail(b.reqs, b.slot, now, exc)
+                continue
+            if finished:
                 for r in b.reqs:
                     r.t_done = now
                     self.inflight_bytes -= r.nbytes
@@ -138,7 +156,11 @@ class Server:
             for r in reqs:
                 r.t_launch = now
                 r.batch = self.batches
-            token = self.engine.launch(slot, key[0], key[1], reqs)
+            try:
+                token = self.engine.launch(slot, key[0], key[1], reqs)
+            except Exception as exc:                   # noqa: BLE001 -- reported per request
+                self._fail(reqs, slot, now, exc)
+                continue
             self.busy.append(_Busy(slot, token, reqs, self.batches))
             self.batches += 1
             self.batch_rows.append(rows)
@@ -166,7 +188,7 @@ class Server:
     def stats(self) -> dict:
         lat = np.array([r.t_done - r.t_arrival for r in self.done])
         if lat.size == 0:
-            return {"requests": 0}
+            return {"requests": 0, "failed": len(self.failed)}
         t_first = min(r.t_arrival for r in self.done)
         t_last = max(r.t_done for r in self.done)
         taps = sum(r.M * r.K * r.L for r in self.done)
@@ -177,7 +199,8 @@ class Server:
                 "p99_ms": float(np.percentile(lat, 99) * 1e3),
                 "max_ms": float(lat.max() * 1e3),
                 "frames_per_s": lat.size / span, "taps_per_s": taps / span,
-                "peak_inflight_bytes": int(self.peak_inflight_bytes)}
+                "peak_inflight_bytes": int(self.peak_inflight_bytes),
+                "failed": len(self.failed)}
 
 
 class _Shape:

@@ -1,5 +1,6 @@
 """Scheduling logic of the serving loop with a fake engine on a virtual clock (no GPU):
-admission by memory, bucketing, batch packing, concurrency limit, latency accounting."""
+admission by memory, bucketing, batch packing, concurrency limit, latency accounting, and
+batches whose engine calls raise (faults injected on the host)."""
 import numpy as np
 
 from paper_2206_05506_gb300.serve import CAPACITIES, Request, Server, kl_class
@@ -122,3 +123,46 @@ def test_poisson_trace_shapes():
     t = np.array([s.t_arrival for s in specs])
     assert np.all(np.diff(t) > 0)
     assert CAPACITIES[-1] >= 4096
+
+
+class FlakyEngine(FakeEngine):
+    """Every `launch_every`-th launch raises; every `done_every`-th launched batch raises
+    when it completes (a device error reported at completion)."""
+
+    def __init__(self, clock, launch_every=5, done_every=7, **kw):
+        super().__init__(clock, **kw)
+        self.launch_every, self.done_every = launch_every, done_every
+        self.calls = 0
+        self.ok = 0
+
+    def launch(self, slot, N, klc, reqs):
+        self.calls += 1
+        if self.calls % self.launch_every == 0:
+            raise RuntimeError("launch refused")
+        tok = super().launch(slot, N, klc, reqs)
+        self.ok += 1
+        tok["fault"] = self.ok % self.done_every == 0
+        return tok
+
+    def done(self, tok):
+        fin = super().done(tok)
+        if fin and tok["fault"]:
+            raise RuntimeError("device error at completion")
+        return fin
+
+
+def test_failing_batches_are_reported_and_the_loop_goes_on():
+    clock = Clock()
+    eng = FlakyEngine(clock, slots=3)
+    srv = Server(eng, mem_cap_bytes=2e6, max_batch_rows=1024)
+    reqs = _requests(dur=0.03, seed=5)
+    st = srv.run(reqs, clock=clock, t0=0.0)
+    ok = {r.rid for r in srv.done}
+    bad = {r.rid for r in srv.failed}
+    assert ok.isdisjoint(bad) and ok | bad == {r.rid for r in reqs}
+    assert st["failed"] == len(bad) > 0 and st["requests"] == len(ok) > 0
+    assert all(r.error.startswith("RuntimeError") for r in srv.failed)
+    assert all(r.error == "" and r.t_done >= r.t_arrival for r in srv.done)
+    # every byte and every stream slot came back
+    assert srv.inflight_bytes == 0
+    assert sorted(srv.free_slots) == list(range(eng.slots)) and not srv.busy
