@@ -165,12 +165,36 @@ def cpu_oracle_sample(bits, Y_sample, K, L, target_s=15.0, max_frames=None):
     return nf, dt, H
 
 
-def run_serving(dev, seconds: float, rate_hz: float = 20000.0):
+def _nmse(est, ref) -> float:
+    est = np.asarray(est).astype(np.complex128)
+    ref = np.asarray(ref).astype(np.complex128)
+    return float(np.sum(np.abs(est - ref) ** 2) / np.sum(np.abs(ref) ** 2))
+
+
+def oracle_references() -> dict:
+    """Part of the cpu_baseline leg: the oracle's results that the serving spot check and
+    the small-case leg compare with.  serving: for every payload of the serving pool, its
+    estimate at all N lags (a request's expected result is the first K*L of them); small:
+    the one-frame launch-latency case."""
+    from oracle import pn_oracle as O
+    from synth import serving as S
+
+    full = {}
+    for (M, N), Yp in S.payload_pool(slots=4, seed=0).items():
+        bits = S.pilot_bits(N)
+        for slot in range(Yp.shape[0]):
+            full[(M, N, slot)] = O.estimate(Yp[[slot]], bits, 1, N)[0, :, 0, :]
+    w = C.SMALL
+    bits, _, Y = C.make(w)
+    return {"serving": full, "small": O.estimate(Y, bits, w.K, w.L)}
+
+
+def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None):
     """Poisson request stream (uneven M, N, K, L) through the continuous-batching server,
-    tensor cores (fp16) and the plain FP32 SIMT path on the same trace."""
+    tensor cores (fp16) and the plain FP32 SIMT path on the same trace.  refs: the oracle's
+    results per payload (from oracle_references) for the spot check, or None."""
     import torch
 
-    from oracle import pn_oracle as O
     from paper_2206_05506_gb300 import serve
     from synth import serving as S
 
@@ -183,13 +207,6 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0):
     checked = [sp for sp in specs if sp.rid % 100 == 0]
     check_buf = torch.zeros(max(1, sum(sp.M * sp.K * sp.L for sp in checked)),
                             dtype=torch.complex64, pin_memory=True)
-    # the oracle's estimate of every payload at all N lags (a request's expected result is
-    # its first K*L lags), computed once per payload
-    full = {}
-    for (M, N), Yp in pool.items():
-        bits = S.pilot_bits(N)
-        for slot in range(Yp.shape[0]):
-            full[(M, N, slot)] = O.estimate(Yp[[slot]], bits, 1, N)[0, :, 0, :]
     res = {"rate_hz": rate_hz, "seconds": seconds, "requests": len(specs)}
     for dtype, name in (("fp16", "fp16_tensor_core"), ("fp32", "fp32_simt")):
         eng = serve.GpuEngine(S.pilot_bits, device=dev, dtype=dtype, slots=4)
@@ -216,15 +233,15 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0):
                                for r in reqs[:200]])            # warm the path
         srv = serve.Server(eng, mem_cap_bytes=40e9)
         st = srv.run(reqs)
-        # accuracy of the sampled requests against the oracle
+        # accuracy of the sampled requests against the oracle's results
         errs = []
-        for r in reqs:
+        for r in reqs if refs is not None else []:
             if r.rid % 100:
                 continue
             n = r.M * r.K * r.L
             H = check_buf[r.coff:r.coff + n].numpy().reshape(r.M, r.K * r.L)
-            want = full[(r.M, r.N, specs[r.rid].slot)][:, :r.K * r.L]
-            errs.append(O.nmse(H, want))
+            want = refs[(r.M, r.N, specs[r.rid].slot)][:, :r.K * r.L]
+            errs.append(_nmse(H, want))
         st["spot_check"] = {"requests": len(errs), "share": len(errs) / max(1, len(reqs)),
                             "nmse_max": float(max(errs)) if errs else None,
                             "nmse_median": float(np.median(errs)) if errs else None}
@@ -310,6 +327,56 @@ def run_yardsticks(dev, bits, Y, pilot, K, L, taps_per_step, reps: int = 20):
         "note": "torch.fft (cuFFT) forward + inverse over all N lags, then the first K*L"}
     del Hc, Pc, H32
     torch.cuda.empty_cache()
+    return out
+
+
+def run_small_case(dev, ref=None, calls: int = 200):
+    """Launch-latency case: one frame of 8 antennas, N = 127, K = 2, L = 16 (8 KB in, 2 KB
+    out), FP32 (the few-lags SIMT kernel).  Per call: the kernel's device time (the
+    library's trace events around the launch), the host wall time of the call and its
+    synchronisation, and end to end from page-locked host memory (pnce_estimate_host: copy
+    in, estimate, copy out).  ref: the oracle's result (from oracle_references) or None."""
+    import torch
+
+    import paper_2206_05506_gb300 as pk
+
+    w = C.SMALL
+    bits, _, Y = C.make(w)
+    Yd = torch.from_numpy(Y).to(dev)
+    pilot = pk.Pilot(bits, device=dev)
+    H = torch.empty((w.F, w.M, w.K, w.L), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(20):
+        pk.estimate(Yd, pilot, w.K, w.L, dtype="fp32", out=H)
+    torch.cuda.synchronize()
+    call_us = []
+    pk.trace_enable(True, dev)
+    pk.trace_read(dev)
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        pk.estimate(Yd, pilot, w.K, w.L, dtype="fp32", out=H)
+        stream.synchronize()
+        call_us.append((time.perf_counter() - t0) * 1e6)
+    dev_us = [t * 1e3 for kind, t in pk.trace_read(dev) if kind == "simt"]
+    pk.trace_enable(False, dev)
+    Yh = torch.from_numpy(Y).pin_memory()
+    Hh = torch.empty((w.F, w.M, w.K, w.L), dtype=torch.complex64).pin_memory()
+    for _ in range(20):
+        pk.estimate_host(Yh, pilot, w.K, w.L, dtype="fp32", out=Hh)
+    e2e_us = []
+    for _ in range(calls):
+        t0 = time.perf_counter()
+        pk.estimate_host(Yh, pilot, w.K, w.L, dtype="fp32", out=Hh)
+        e2e_us.append((time.perf_counter() - t0) * 1e6)
+    out = {"workload": w.name, "dtype": "fp32", "calls": calls,
+           "kernel_us_median": float(np.median(dev_us)),
+           "call_us_median": float(np.median(call_us)),
+           "e2e_host_us_median": float(np.median(e2e_us)),
+           "e2e_host_us_p99": float(np.percentile(e2e_us, 99)),
+           "taps": w.F * w.M * w.K * w.L,
+           "e2e_matches_device_result": bool(torch.equal(Hh, H.cpu()))}
+    if ref is not None:
+        out["nmse_vs_oracle"] = _nmse(H.cpu().numpy(), ref)
     return out
 
 
@@ -412,6 +479,8 @@ def main():
                     help="also time the relaxed-pilot forward + adjoint (1/0)")
     ap.add_argument("--yardsticks", type=int, default=1,
                     help="time the O(N log N) yardsticks (fast m-sequence transform, cuFFT)")
+    ap.add_argument("--small-case", type=int, default=1,
+                    help="time the one-frame launch-latency case (1/0)")
     ap.add_argument("--other-dtypes", type=int, default=1,
                     help="also time the other arithmetics on the same batch (1/0)")
     args = ap.parse_args()
@@ -580,8 +649,13 @@ def main():
                "kind": "oracle",
                "sample": f"first {nf} of {F} frames, FP64 Toeplitz product (numpy BLAS)"}
         nmse = O.nmse(H[:nf].cpu().numpy(), Href)
+        refs = oracle_references()
+    else:
+        refs = {}
 
-    serving = run_serving(dev, args.serving_seconds) if args.serving_seconds > 0 else None
+    serving = (run_serving(dev, args.serving_seconds, refs=refs.get("serving"))
+               if args.serving_seconds > 0 else None)
+    small = run_small_case(dev, ref=refs.get("small")) if args.small_case else None
     differentiation = run_differentiation(dev) if args.differentiation else None
 
     # the other arithmetics on the same batch (shorter runs, same step definition)
@@ -634,6 +708,7 @@ def main():
         "nmse_vs_oracle": nmse,
         "cpu_baseline": cpu,
         "serving": serving,
+        "small_case": small,
         "other_dtypes": others,
         "differentiation": differentiation,
         "yardsticks": yard,
