@@ -110,3 +110,20 @@ def test_product_code_does_not_import_the_oracle():
         for f in files:
             if f.endswith(".py"):
                 assert not pat.search(open(os.path.join(dirpath, f)).read()), f
+
+
+def test_empty_and_degenerate_shapes_rejected_up_front(lib):
+    # F = 0 or M = 0 (empty batch), N < 2, K or L = 0, and K*L > N (Eq. 7) are PNCE_EINVAL
+    # and need no workspace; the shape is checked before any pointer is used, so stand-in
+    # addresses are never dereferenced
+    dummy = C.c_void_p(256)
+    for F, M, N, K, L in [(0, 4, 127, 1, 8), (1, 0, 127, 1, 8), (1, 4, 1, 1, 1),
+                          (1, 4, 127, 0, 8), (1, 4, 127, 1, 0), (1, 4, 127, 2, 64)]:
+        for dt in (1, 2, 3, 4):
+            assert lib.pnce_workspace_size(F, M, N, K, L, dt) == 0
+        assert lib.pnce_backward_workspace_size(F, M, N, K, L) == 0
+        for dt in (0, 2):
+            assert lib.pnce_estimate(dummy, dummy, dummy, F, M, N, K, L, dt, dummy, 1 << 30,
+                                     dummy, None) == 1
+    # the full-lag case K*L = N is admissible
+    assert lib.pnce_workspace_size(1, 4, 127, 1, 127, 2) > 0
