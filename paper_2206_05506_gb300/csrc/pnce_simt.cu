@@ -268,9 +268,11 @@ cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, lo
     cudaError_t e = cudaFuncSetAttribute(simt_corr_kernel<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // Antenna groups: at least ceil(A / TA), raised so that the grid fills whole waves of the
-    // resident blocks (tiles of 2^k rows leave the last wave partly empty on 152 SMs).  The
-    // grouping changes no result: every output is summed over n in the same order.
+    // Antenna groups: ceil(A / TA); for a grid that fills at least half of the resident
+    // blocks, raised so that it fills whole waves (tiles of 2^k rows leave the last wave
+    // partly empty on 152 SMs).  Small grids keep full groups, so that small batches running
+    // side by side on several streams each stay on a few SMs.  The grouping changes no
+    // result: every output is summed over n in the same order.
     long long groups = (A + TA - 1) / TA;
     int dev = 0, sms = 0, per_sm = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -279,8 +281,8 @@ cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, lo
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_corr_kernel<MODE>, 256,
                                                            smem)) != cudaSuccess)
         return e;
-    if (sms > 0 && per_sm > 0) {
-        const long long slots = (long long)sms * per_sm;
+    const long long slots = (long long)sms * per_sm;
+    if (slots > 0 && 2 * groups * num_jt >= slots) {
         const long long waves = (groups * num_jt + slots - 1) / slots;
         const long long even = waves * slots / num_jt;
         groups = std::min(A, std::max(groups, even));
