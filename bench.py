@@ -171,6 +171,17 @@ def _nmse(est, ref) -> float:
     return float(np.sum(np.abs(est - ref) ** 2) / np.sum(np.abs(ref) ** 2))
 
 
+# Received blocks of the serving trace: 32 per (M, N) shape, 471 MB in all (3.6x L2), handed
+# to the requests of each shape in turn, so that a request's block was last read about 512
+# requests (~470 MB of other blocks) earlier and comes over the host link, not from L2.
+SERVING_SLOTS = 32
+
+
+def serving_payloads():
+    from synth import serving as S
+    return S.payload_pool(slots=SERVING_SLOTS, seed=0)
+
+
 def oracle_references() -> dict:
     """Part of the cpu_baseline leg: the oracle's results that the serving spot check and
     the small-case leg compare with.  serving: for every payload of the serving pool, its
@@ -180,7 +191,7 @@ def oracle_references() -> dict:
     from synth import serving as S
 
     full = {}
-    for (M, N), Yp in S.payload_pool(slots=4, seed=0).items():
+    for (M, N), Yp in serving_payloads().items():
         bits = S.pilot_bits(N)
         for slot in range(Yp.shape[0]):
             full[(M, N, slot)] = O.estimate(Yp[[slot]], bits, 1, N)[0, :, 0, :]
@@ -198,9 +209,13 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None):
     from paper_2206_05506_gb300 import serve
     from synth import serving as S
 
-    pool = S.payload_pool(slots=4, seed=0)
+    pool = serving_payloads()
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in pool.items()}
-    specs = S.poisson_trace(rate_hz, seconds, seed=0, payload_slots=4)
+    specs = S.poisson_trace(rate_hz, seconds, seed=0, payload_slots=SERVING_SLOTS)
+    turn = {}
+    for sp in specs:                           # each shape's blocks in turn (see SERVING_SLOTS)
+        sp.slot = turn.get((sp.M, sp.N), 0)
+        turn[(sp.M, sp.N)] = (sp.slot + 1) % SERVING_SLOTS
     ring_elems = 64 << 20                      # 512 MB of page-locked results, reused in turn
     ring = torch.zeros(ring_elems, dtype=torch.complex64, pin_memory=True)
     # spot check: every 100th request keeps its result in a buffer of its own
