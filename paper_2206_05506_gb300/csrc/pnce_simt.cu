@@ -5,9 +5,10 @@
 // with p'[x] = p[-x mod N].  In general: out[a][o] = scale * sum_{k < Kred} in[a][k] *
 // pilot[(k - o) mod Nmod], o < Nout.
 //
-// Block tile: up to 32 antennas x 256 lags (the rows are split into balanced groups so that
-// the grid fills whole waves); thread tile: 4 antennas x 8 consecutive lags, so each
-// received sample read from shared memory feeds 64 FMAs.  Because a thread's lags
+// Block tile: up to 32 antennas x 256 lags (for large grids the rows are split into
+// balanced groups so that the grid fills whole waves); thread tile: 4 antennas x 8
+// consecutive lags, so each received sample read from shared memory feeds 64 FMAs.  Grids
+// smaller than half the GPU use 1 antenna per thread (8-row blocks, 4x shorter).  Because a thread's lags
 // are consecutive, the pilot values it needs at sample n+1 are those of sample n shifted
 // by one lag: a 15-entry register window slides along the pilot, one new shared load per
 // sample.  Received samples and the pilot window of each 128-sample chunk are staged in
@@ -18,10 +19,8 @@
 
 namespace {
 
-constexpr int RA = 4;             // antennas per thread
 constexpr int RJ = 8;             // consecutive lags per thread
 constexpr int WARPS = 8;
-constexpr int TA = WARPS * RA;    // antennas per block
 constexpr int TJ = 32 * RJ;       // lags per block
 constexpr int NC = 128;           // samples per chunk
 constexpr int ELEN = NC + TJ + 8; // pilot entries staged per chunk
@@ -41,11 +40,14 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
 
+// RA antennas per thread (4; 1 for small grids), WARPS * RA antennas per block
+template <int RA>
 struct Smem {
     float e[2][EPAD];
-    float2 y[2][TA][NC];
+    float2 y[2][WARPS * RA][NC];
 };
-static_assert(offsetof(Smem, y) % 16 == 0 && NC % 2 == 0, "paired sample loads need 16-byte rows");
+static_assert(offsetof(Smem<4>, y) % 16 == 0 && offsetof(Smem<1>, y) % 16 == 0 && NC % 2 == 0,
+              "paired sample loads need 16-byte rows");
 
 // FWD_BITS: +-1 pilot from packed bits.  FWD_REAL / ADJ_REAL: float pilot, read forwards
 // or backwards.  *_TANH: the float argument is theta and the pilot is tanh(theta).
@@ -65,14 +67,15 @@ __device__ __forceinline__ float pilot_value(const uint32_t* bits, const float* 
     }
 }
 
-template <int MODE>
+template <int MODE, int RA>
 __global__ void __launch_bounds__(256, 2)
 simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ preal,
                  const float2* __restrict__ Y, long long y_stride, long long A,
                  int N /* reduction length */, const pnce::LagMap lags, int nmod, int num_jt,
                  long long groups, float invN, float2* __restrict__ H) {
+    constexpr int TA = WARPS * RA;    // antennas per block
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem& sm = *reinterpret_cast<Smem*>(smem_raw);
+    Smem<RA>& sm = *reinterpret_cast<Smem<RA>*>(smem_raw);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long bid = blockIdx.x;
@@ -256,6 +259,23 @@ cudaError_t launch_few_lags(const uint32_t* ext, const float2* Y, long long y_st
 
 constexpr int FEW_LAGS = 32;    // largest K*L the few-lags kernel takes
 
+template <int MODE, int RA>
+cudaError_t launch_ra(const uint32_t* bits, const float* preal, const float2* Y,
+                      long long y_stride, long long A, int N, const pnce::LagMap& lags, int nmod,
+                      int num_jt, long long groups, float2* H, cudaStream_t s) {
+    const long long blocks = (long long)num_jt * groups;
+    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    const size_t smem = sizeof(Smem<RA>);
+    cudaError_t e = cudaFuncSetAttribute(simt_corr_kernel<MODE, RA>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const float invN = (float)(1.0 / (double)nmod);
+    simt_corr_kernel<MODE, RA><<<(unsigned)blocks, 256, smem, s>>>(bits, preal, Y, y_stride, A, N,
+                                                                   lags, nmod, num_jt, groups,
+                                                                   invN, H);
+    return cudaGetLastError();
+}
+
 template <int MODE>
 cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, long long y_stride,
                    long long A, int N, const pnce::LagMap& lags, int nmod, float2* H,
@@ -264,36 +284,35 @@ cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, lo
     if (num_jt_ll > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int num_jt = (int)num_jt_ll;
     if (A <= 0 || num_jt <= 0) return cudaSuccess;
-    const size_t smem = sizeof(Smem);
-    cudaError_t e = cudaFuncSetAttribute(simt_corr_kernel<MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    // Antenna groups: ceil(A / TA); for a grid that fills at least half of the resident
-    // blocks, raised so that it fills whole waves (tiles of 2^k rows leave the last wave
-    // partly empty on 152 SMs).  Small grids keep full groups, so that small batches running
-    // side by side on several streams each stay on a few SMs.  The grouping changes no
-    // result: every output is summed over n in the same order.
-    long long groups = (A + TA - 1) / TA;
     int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
         return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_corr_kernel<MODE>, 256,
-                                                           smem)) != cudaSuccess)
+    if ((e = cudaFuncSetAttribute(simt_corr_kernel<MODE, 4>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)sizeof(Smem<4>))) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, simt_corr_kernel<MODE, 4>, 256,
+                                                           sizeof(Smem<4>))) != cudaSuccess)
         return e;
     const long long slots = (long long)sms * per_sm;
-    if (slots > 0 && 2 * groups * num_jt >= slots) {
+    long long groups = (A + 4 * WARPS - 1) / (4 * WARPS);
+    if (slots > 0 && 2 * groups * num_jt < slots) {
+        // A small grid (less than half of the resident 32-row blocks): blocks of 8 rows, one
+        // antenna per thread, so each block is 4x shorter and a small batch finishes sooner.
+        return launch_ra<MODE, 1>(bits, preal, Y, y_stride, A, N, lags, nmod, num_jt,
+                                  (A + WARPS - 1) / WARPS, H, s);
+    }
+    // Otherwise 32-row groups, raised so that the grid fills whole waves of the resident
+    // blocks (tiles of 2^k rows leave the last wave partly empty on 152 SMs).  Neither choice
+    // changes a result: every output is summed over n in the same order.
+    if (slots > 0) {
         const long long waves = (groups * num_jt + slots - 1) / slots;
         const long long even = waves * slots / num_jt;
         groups = std::min(A, std::max(groups, even));
     }
-    const long long blocks = (long long)num_jt * groups;
-    if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-    const float invN = (float)(1.0 / (double)nmod);
-    simt_corr_kernel<MODE><<<(unsigned)blocks, 256, smem, s>>>(bits, preal, Y, y_stride, A, N,
-                                                               lags, nmod, num_jt, groups, invN,
-                                                               H);
-    return cudaGetLastError();
+    return launch_ra<MODE, 4>(bits, preal, Y, y_stride, A, N, lags, nmod, num_jt, groups, H, s);
 }
 
 }  // namespace
