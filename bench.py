@@ -345,6 +345,39 @@ def run_yardsticks(dev, bits, Y, pilot, K, L, taps_per_step, reps: int = 20):
     return out
 
 
+def run_layouts(dev, pilot, Y, K, L, taps_per_step, reps: int = 30):
+    """The pilot-slot layouts on the same batch (fp16): rows with an L-sample cyclic prefix
+    in front (the prefix repeats the block's tail), and the even-spread shift rule
+    k * floor(N / K) of Eq. 8.  ms per step beside the plain step's."""
+    import torch
+
+    import paper_2206_05506_gb300 as pk
+
+    F, M, N = Y.shape
+    Ycp = torch.empty((F, M, N + L), dtype=torch.complex64, device=dev)
+    Ycp[:, :, L:] = Y
+    Ycp[:, :, :L] = Y[:, :, N - L:]
+    H = torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, src, kw in (("cyclic_prefix", Ycp, {"cp_len": L}),
+                          ("spread_shifts", Y, {"shift_rule": "spread"})):
+        for _ in range(3):
+            pk.estimate(src, pilot, K, L, dtype="fp16", out=H, **kw)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            pk.estimate(src, pilot, K, L, dtype="fp16", out=H, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms_per_step": ms, "value": taps_per_step / (ms / 1e3)}
+    del Ycp
+    assert pk.get_status(dev) == 0
+    return out
+
+
 def run_small_case(dev, ref=None, calls: int = 200):
     """Launch-latency case: one frame of 8 antennas, N = 127, K = 2, L = 16 (8 KB in, 2 KB
     out), FP32 (the few-lags SIMT kernel).  Per call: the kernel's device time (the
@@ -494,6 +527,8 @@ def main():
                     help="also time the relaxed-pilot forward + adjoint (1/0)")
     ap.add_argument("--yardsticks", type=int, default=1,
                     help="time the O(N log N) yardsticks (fast m-sequence transform, cuFFT)")
+    ap.add_argument("--layouts", type=int, default=1,
+                    help="time the cyclic-prefix and even-spread pilot layouts (1/0)")
     ap.add_argument("--small-case", type=int, default=1,
                     help="time the one-frame launch-latency case (1/0)")
     ap.add_argument("--other-dtypes", type=int, default=1,
@@ -695,6 +730,8 @@ def main():
         assert pk.get_status(dev) == 0
 
     yard = run_yardsticks(dev, bits, Y, pilot, K, L, taps_per_step) if args.yardsticks else None
+    layouts = (run_layouts(dev, pilot, Y, K, L, taps_per_step)
+               if args.layouts and dt == "fp16" else None)
 
     line = {
         "metric": "CIR taps estimated/s", "value": value, "unit": "taps/s", "n_gpus": world,
@@ -727,6 +764,7 @@ def main():
         "other_dtypes": others,
         "differentiation": differentiation,
         "yardsticks": yard,
+        "layouts": layouts,
     }
     print(json.dumps(line), flush=True)
     if world > 1:
