@@ -47,16 +47,20 @@ def load_peaks():
     return FALLBACK_PEAKS, "fallback"
 
 
-def src_hash() -> str:
-    """Hash of the tensor-core kernel source with comments and whitespace removed, so that
-    a recorded ncu traffic figure stays valid across comment edits but not code edits."""
+def source_hash(text: str) -> str:
+    """Hash of C/CUDA source with comments and whitespace removed."""
     import re
-    with open(os.path.join(ROOT, "paper_2206_05506_gb300", "csrc", "pnce_tc.cu")) as fh:
-        text = fh.read()
     text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
     text = re.sub(r"//[^\n]*", " ", text)
     text = " ".join(text.split())
     return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
+def src_hash() -> str:
+    """Hash of the tensor-core kernel source, so that a recorded ncu traffic figure stays
+    valid across comment edits but not code edits."""
+    with open(os.path.join(ROOT, "paper_2206_05506_gb300", "csrc", "pnce_tc.cu")) as fh:
+        return source_hash(fh.read())
 
 
 def traffic_from_profile(workload: str, dtype: str, frames: int):
@@ -125,10 +129,15 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        lo, hi = self.t0, self.t1 + self.PERIOD_MS / 1000.0
+        return self.summarize(list(self.lines), self.t0, self.t1 + self.PERIOD_MS / 1000.0)
+
+    @staticmethod
+    def summarize(lines, lo: float, hi: float):
+        """Median SM clock, maximum clock, median power and the throttle reasons seen
+        active among the (time, csv line) samples taken in [lo, hi]."""
         sm, mx, power, reasons = [], None, [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for t, line in list(self.lines):
+        for t, line in lines:
             if not (lo <= t <= hi):
                 continue
             r = [x.strip() for x in line.split(",")]
