@@ -19,7 +19,10 @@ taps) whose received blocks sit in page-locked host memory.  The loop
   minus scheduled arrival;
 * if the engine raises while launching or polling a batch, that batch's requests are
   recorded as failed (with the error), their memory and stream slot are released, and the
-  loop goes on with the rest.
+  loop goes on with the rest;
+* at the end of a run it asks the engine (if the engine can tell) whether any kernel
+  latched an error on the device -- a bounded wait that ran out, an invalid descriptor --
+  and raises if one did, since some results may then be wrong.
 
 Pilot tables and the per-shape buffers stay resident on the device.  Each request's result
 depends only on its own antenna rows (per-antenna scales, fixed reduction order), so it is
@@ -35,7 +38,7 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import DTYPES, Pilot, _lib, context, estimate_grouped, grouped_workspace_size
+from . import DTYPES, Pilot, _lib, check, context, estimate_grouped, grouped_workspace_size
 
 KL_CLASSES = (64, 256, 1024)
 CAPACITIES = (64, 256, 1024, 4096)        # antennas per batch
@@ -183,6 +186,9 @@ class Server:
                 self.submit(requests[i])
                 i += 1
             self.poll(now)
+        engine_check = getattr(self.engine, "check", None)
+        if engine_check is not None:
+            engine_check()
         return self.stats()
 
     def stats(self) -> dict:
@@ -310,3 +316,9 @@ class GpuEngine:
     @staticmethod
     def done(token) -> bool:
         return token.query()
+
+    def check(self):
+        """Raise PnceError if a kernel of the batches run so far latched an error status
+        (reads and clears the handle's status word; waits for the device)."""
+        torch.cuda.synchronize(self.device)
+        check(self.ctx.status(), "serving batches")

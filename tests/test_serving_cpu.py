@@ -166,3 +166,21 @@ def test_failing_batches_are_reported_and_the_loop_goes_on():
     # every byte and every stream slot came back
     assert srv.inflight_bytes == 0
     assert sorted(srv.free_slots) == list(range(eng.slots)) and not srv.busy
+
+
+class LatchingEngine(FakeEngine):
+    """Reports, when asked at the end of a run, an error latched on the device."""
+
+    def check(self):
+        raise RuntimeError("device status: a wait ran out")
+
+
+def test_a_latched_device_error_is_raised_at_the_end_of_the_run():
+    import pytest
+    clock = Clock()
+    eng = LatchingEngine(clock, slots=2)
+    srv = Server(eng)
+    reqs = _requests(dur=0.005)
+    with pytest.raises(RuntimeError, match="wait ran out"):
+        srv.run(reqs, clock=clock, t0=0.0)
+    assert len(srv.done) == len(reqs)          # every batch ran before the check
