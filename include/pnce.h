@@ -251,7 +251,7 @@ pnce_status pnce_trace_read(pnce_handle* h, int* kinds, float* ms, int max_entri
  *   source row pitch src_pitch elements (counts are clamped to src_pitch).
  */
 /*
- * Grouped estimate for serving (§ continuous batching; the paper processes one frame at a
+ * Grouped estimate for continuous-batching serving (the paper processes one frame at a
  * time, so this has no counterpart there): the antennas of nreq requests that share one
  * pilot (same N) are estimated as one batch of `rows` rows with kl_max lags.  descs is a
  * table of nreq <= rows descriptors in device memory or page-locked host memory, copied
