@@ -1,8 +1,8 @@
 """FP64 CPU oracle for PN-sequence correlation channel estimation.
 
 TEST INFRASTRUCTURE ONLY.  Nothing on the product path may import, call or link this
-module: only the tests, the smoke check in __graft_entry__ and the CPU-baseline leg
-of bench.py use it.  It shares no code with the CUDA library.
+module: only the tests, the smoke check in __graft_entry__, and bench.py's CPU-baseline
+leg and its reference arm use it.  It shares no code with the CUDA library.
 
 Everything is plain numpy in float64 (complex128), written from the paper's
 definitions so that it can be checked by eye:
