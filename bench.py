@@ -698,10 +698,13 @@ def main():
                 "kernel": "tc_corr_kernel", "peak_source":
                 f"{peak_src} {'sustained' if long_region else 'burst'} bf16 x {DTYPE_RATIO[dt]}"}
 
-    # ---- CPU baseline (FP64 oracle) on a frame sample, plus accuracy of those frames
+    # ---- CPU baseline (FP64 oracle) on a frame sample, plus accuracy of those frames.  It
+    # and the legs below describe the single-GPU configuration: they run at N = 1 only
+    # (with N > 1 they would keep every GPU of the job idle for minutes).
+    single = world == 1
     cpu = None
     nmse = None
-    if not args.no_cpu:
+    if not args.no_cpu and single:
         from oracle import pn_oracle as O
         nf, cdt, Href = cpu_oracle_sample(bits, Y_host, K, L)
         cpu = {"value": nf * M * K * L / cdt, "unit": "taps/s", "cores": host_cores(),
@@ -713,13 +716,13 @@ def main():
         refs = {}
 
     serving = (run_serving(dev, args.serving_seconds, refs=refs.get("serving"))
-               if args.serving_seconds > 0 else None)
-    small = run_small_case(dev, ref=refs.get("small")) if args.small_case else None
-    differentiation = run_differentiation(dev) if args.differentiation else None
+               if args.serving_seconds > 0 and single else None)
+    small = run_small_case(dev, ref=refs.get("small")) if args.small_case and single else None
+    differentiation = run_differentiation(dev) if args.differentiation and single else None
 
     # the other arithmetics on the same batch (shorter runs, same step definition)
     others = {}
-    if args.other_dtypes:
+    if args.other_dtypes and single:
         for odt in [d for d in ("e4m3", "bf16", "tf32", "fp16", "fp32") if d != dt]:
             ows = (torch.empty(pk.workspace_size(F, M, N, K, L, odt), dtype=torch.uint8,
                                device=dev) if odt != "fp32" else None)
@@ -738,9 +741,10 @@ def main():
             del ows
         assert pk.get_status(dev) == 0
 
-    yard = run_yardsticks(dev, bits, Y, pilot, K, L, taps_per_step) if args.yardsticks else None
+    yard = (run_yardsticks(dev, bits, Y, pilot, K, L, taps_per_step)
+            if args.yardsticks and single else None)
     layouts = (run_layouts(dev, pilot, Y, K, L, taps_per_step)
-               if args.layouts and dt == "fp16" else None)
+               if args.layouts and dt == "fp16" and single else None)
 
     line = {
         "metric": "CIR taps estimated/s", "value": value, "unit": "taps/s", "n_gpus": world,
