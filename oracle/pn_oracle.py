@@ -212,18 +212,22 @@ def round_to_format(x, fmt: str) -> np.ndarray:
 def antenna_scale_exponents(Y, fmt: str) -> np.ndarray:
     """Per-antenna power-of-two scale exponent s_e (scale = 2^s_e), int32 [F, M].
 
-    A = max_n max(|Re y[n]|, |Im y[n]|); for fp16 / e4m3, s_e = t - E where
-    A = m 2^E, m in [0.5, 1), so that the scaled peak lies in [2^(t-1), 2^t); for bf16,
-    tf32 and fp32, and for A = 0, s_e = 0.  s_e is clamped to [-100, 100].
+    A = max_n max(|Re y[n]|, |Im y[n]|) over the parts that are numbers (a NaN part is
+    left out of the peak); for fp16 / e4m3, s_e = t - E where A = m 2^E, m in [0.5, 1),
+    so that the scaled peak lies in [2^(t-1), 2^t); for bf16, tf32 and fp32, and for a
+    peak that is 0 or not finite (an infinite part, or no number at all), s_e = 0, i.e.
+    scale 1.  s_e is clamped to [-100, 100].
     """
     Y = np.asarray(Y)
     t = SCALE_TARGET_EXP[fmt]
     F, M, _ = Y.shape
     if t is None:
         return np.zeros((F, M), dtype=np.int32)
-    A = np.maximum(np.abs(Y.real), np.abs(Y.imag)).max(axis=-1).astype(np.float64)
-    _, E = np.frexp(A)
-    se = np.where(A > 0, t - E, 0)
+    parts = np.fmax(np.abs(Y.real), np.abs(Y.imag)).astype(np.float64)   # fmax skips NaN
+    A = np.fmax.reduce(parts, axis=-1)
+    ok = np.isfinite(A) & (A > 0)
+    _, E = np.frexp(np.where(ok, A, 1.0))
+    se = np.where(ok, t - E, 0)
     return np.clip(se, -100, 100).astype(np.int32)
 
 

@@ -328,6 +328,19 @@ def test_scale_exponents():
     assert np.all(peak[:3] >= 128) and np.all(peak[:3] < 256)
 
 
+def test_scale_exponents_of_non_finite_peaks():
+    # reading of the paper's silence on bad samples: a peak that is 0 or not finite gives
+    # scale 1; a NaN part is left out of the peak
+    Y = np.zeros((1, 4, 3), np.complex64)
+    Y[0, 0] = [1.0, np.inf, 0.5]                     # infinite peak -> scale 1
+    Y[0, 1] = [np.nan, 0.75, -0.25j]                  # NaN left out: peak 0.75
+    Y[0, 2] = [complex(np.nan, np.nan)] * 3           # no number at all -> scale 1
+    Y[0, 3] = [complex(0.0, -np.inf), 0, 0]
+    for fmt, t in (("fp16", 15), ("e4m3", 8)):
+        se = O.antenna_scale_exponents(Y, fmt)[0]
+        assert list(se) == [0, t, 0, 0]
+
+
 def test_quantized_estimate_within_stated_tolerances():
     bits, _, Y = _small_case(10, 16, 4, 64, 2, seed=9, snr=10.0)
     ref = O.estimate(Y, bits, 4, 64)
