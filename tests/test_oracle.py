@@ -358,6 +358,23 @@ def test_mae_eq12():
     assert O.nmse(h, h) == 0.0
 
 
+def test_nmse_hand_cases():
+    # est = [3, 0], ref = [1, 1]: errors 2 and -1, so sum|e|^2 = 5 over sum|ref|^2 = 2.
+    # Unsquared terms would give 3/2 = 1.5, dividing by sum|est|^2 would give 5/9.
+    assert O.nmse(np.array([3.0, 0.0]), np.array([1.0, 1.0])) == 2.5
+    # complex entries: est = [1+2i, 3i], ref = [1, 4i] -> errors 2i and -i, sum|e|^2 = 5;
+    # sum|ref|^2 = 1 + 16 = 17 (not |1 + 4i|^2 summed per part wrongly as 1 + 4).
+    assert O.nmse(np.array([1 + 2j, 3j]), np.array([1.0, 4j])) == pytest.approx(5 / 17, abs=0)
+    # the metric is not symmetric: swapping the arguments changes the denominator
+    assert O.nmse(np.array([1.0, 1.0]), np.array([3.0, 0.0])) == pytest.approx(5 / 9, abs=1e-15)
+    # scaling both by the same factor leaves it unchanged (a ratio of like powers)
+    assert O.nmse(np.array([30.0, 0.0]), np.array([10.0, 10.0])) == 2.5
+    # shape is irrelevant: the sums run over all entries of a launch
+    e = np.array([[[[3.0]], [[0.0]]]])
+    r = np.array([[[[1.0]], [[1.0]]]])
+    assert O.nmse(e, r) == 2.5
+
+
 # ------------------------------------------- cyclic prefix and shift rules (Sec. II)
 
 
