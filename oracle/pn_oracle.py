@@ -188,13 +188,21 @@ def round_to_format(x, fmt: str) -> np.ndarray:
     """Round float64 values to the nearest value of a binary format, by definition.
 
     The grid spacing at |x| is 2^(max(e, emin) - mbits) with e = floor(log2|x|); values
-    are rounded to that grid (ties to even, or away from zero for tf32) and saturated
-    at the largest finite value.
+    are rounded to that grid (ties to even, or away from zero for tf32).  A rounded
+    magnitude above the largest finite value overflows as IEEE 754 rounding to nearest
+    prescribes: to infinity for the formats that have one (fp16, bf16, tf32); e4m3 has
+    no infinity and saturates at 448 instead (the satfinite convention).  Infinite inputs
+    follow the same rule (inf for fp16 / bf16 / tf32, +-448 for e4m3); NaN stays NaN.
     """
     mbits, emin, vmax, ties = FORMATS[fmt]
     x = np.asarray(x, dtype=np.float64)
-    out = np.zeros_like(x)
-    nz = x != 0
+    top = vmax if fmt == "e4m3" else np.inf     # where an overflowing magnitude lands
+    out = np.full(x.shape, np.nan)              # NaN stays NaN
+    inf = np.isinf(x)
+    out[inf] = np.sign(x[inf]) * top
+    fin = np.isfinite(x)
+    out[fin & (x == 0)] = 0.0
+    nz = fin & (x != 0)
     ax = np.abs(x[nz])
     _, E = np.frexp(ax)                         # ax = m 2^E, m in [0.5, 1)
     e = np.maximum(E - 1, emin)
@@ -204,7 +212,8 @@ def round_to_format(x, fmt: str) -> np.ndarray:
         rq = np.rint(q)                         # round half to even
     else:
         rq = np.floor(q + 0.5)                  # round half away from zero
-    v = np.minimum(rq * ulp, vmax)
+    v = rq * ulp
+    v = np.where(v > vmax, top, v)
     out[nz] = np.sign(x[nz]) * v
     return out
 
@@ -240,13 +249,21 @@ def quantize(Y, fmt: str):
     Y = np.asarray(Y)
     se = antenna_scale_exponents(Y, fmt)
     s = np.ldexp(1.0, se)[..., None]
-    re = round_to_format(Y.real.astype(np.float64) * s, fmt)
-    im = round_to_format(Y.imag.astype(np.float64) * s, fmt)
-    return re + 1j * im, se
+    Q = np.empty(Y.shape, dtype=np.complex128)
+    # assembled part by part: re + 1j * im would turn an infinite imaginary part into a
+    # NaN real part (1j * inf = nan + inf j in complex arithmetic)
+    Q.real = round_to_format(Y.real.astype(np.float64) * s, fmt)
+    Q.imag = round_to_format(Y.imag.astype(np.float64) * s, fmt)
+    return Q, se
 
 
 def dequantize(Q, se) -> np.ndarray:
-    return Q * np.ldexp(1.0, -np.asarray(se))[..., None]
+    """Undo the exact per-antenna scale, part by part (see quantize)."""
+    s = np.ldexp(1.0, -np.asarray(se))[..., None]
+    out = np.empty(np.broadcast_shapes(Q.shape, s.shape), dtype=np.complex128)
+    out.real = Q.real * s
+    out.imag = Q.imag * s
+    return out
 
 
 def estimate_quantized(Y, bits, K: int, L: int, fmt: str) -> np.ndarray:

@@ -127,6 +127,48 @@ def test_quantizer_bit_exact(pk, shape, dtype):
     assert np.allclose(res["power"].cpu().numpy(), pw, rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("dtype", TC)
+def test_quantizer_non_finite_samples(pk, dtype):
+    # samples that are not numbers are ordinary data here: a NaN part is left out of the
+    # antenna's peak, an infinite part (or no number at all) gives scale 1, and each part
+    # is then rounded as IEEE 754 prescribes (infinity for fp16 / bf16 / tf32, +-448 for
+    # e4m3); an all-zero antenna gets scale 1 and zero codes
+    rng = np.random.default_rng(21)
+    N = 67                                       # ragged: 16 groups of 4 and a tail of 3
+    M = 11                                       # a ragged second 8-antenna group
+    Y = ((rng.standard_normal((1, M, N)) + 1j * rng.standard_normal((1, M, N))) * 0.3)
+    Y = Y.astype(np.complex64)
+    Y[0, 0, 5] = complex(1.0, np.inf)           # an infinite part: scale 1
+    Y[0, 1, [0, 9, 66]] = complex(np.nan, 0.5)  # NaN parts left out of the peak
+    Y[0, 1, 33] = complex(-0.75, np.nan)
+    Y[0, 2, :] = complex(np.nan, np.nan)        # no number at all: scale 1
+    Y[0, 3, 64] = complex(0.0, -np.inf)         # in the ragged tail
+    Y[0, 4, :] = 0.0                            # all zero: scale 1
+    Y[0, 5, :] *= np.float32(1e-30)             # tiny but finite: a large scale
+    dev = torch.device("cuda", 0)
+    res = pk.quantize(torch.from_numpy(Y).to(dev), dtype, want_power=True)
+    Q, se = O.quantize(Y, dtype)
+    t = O.SCALE_TARGET_EXP[dtype]
+    if t is not None:
+        peak1 = np.nanmax(np.abs(np.stack([Y[0, 1].real, Y[0, 1].imag])))
+        assert list(se[0, :5]) == [0, t - int(np.frexp(np.float64(peak1))[1]), 0, 0, 0]
+        assert se[0, 5] == 100                   # the clamp
+    rows = _decode(res["q"], dtype)[:, :N]
+    a = np.arange(M)
+    re_rows = 16 * (a // 8) + a % 8
+    got = np.stack([rows[re_rows], rows[re_rows + 8]], axis=1)
+    want = np.stack([Q.real, Q.imag], axis=-2).reshape(M, 2, N)
+    assert np.array_equal(got, want, equal_nan=True)   # NaN at the same places
+    pad = np.setdiff1d(np.arange(rows.shape[0]), np.concatenate([re_rows, re_rows + 8]))
+    assert np.all(rows[pad] == 0)
+    assert np.array_equal(res["exps"].cpu().numpy(), se.reshape(-1))
+    fac = np.float32(1.0 / N) * np.ldexp(np.float32(1.0), -se.reshape(-1)).astype(np.float32)
+    assert np.array_equal(res["factor"].cpu().numpy(), fac)
+    pw = (np.abs(Y.astype(np.complex128)) ** 2).mean(axis=-1).reshape(-1)
+    assert np.allclose(res["power"].cpu().numpy(), pw, rtol=1e-12, atol=0, equal_nan=True)
+    assert pk.get_status(dev) == 0
+
+
 def test_tensor_core_staged_pilot_path(pk, monkeypatch):
     # the per-stage pilot generator (used when the resident list does not fit) on shapes
     # with several K blocks, lag tiles and a ragged row tile

@@ -294,6 +294,48 @@ def test_round_matches_torch_cast(fmt, tdt):
     assert np.array_equal(O.round_to_format(v, fmt), want)
 
 
+@pytest.mark.parametrize("fmt,tdt", [("fp16", "float16"), ("bf16", "bfloat16")])
+def test_round_overflow_and_non_finite_match_torch_cast(fmt, tdt):
+    # IEEE 754 round to nearest past the largest finite value: the first magnitude that
+    # rounds up out of the top binade becomes infinity; infinities and NaN pass through
+    torch = pytest.importorskip("torch")
+    vmax = O.FORMATS[fmt][2]
+    mbits = O.FORMATS[fmt][0]
+    half_ulp = np.ldexp(1.0, int(np.frexp(vmax)[1]) - 1 - mbits - 1)
+    v = np.array([vmax, vmax + half_ulp, np.nextafter(np.float32(vmax + half_ulp), np.float32(0)),
+                  1e30, np.float32(3.0e38), np.inf, -np.inf, -1e30, np.nan],
+                 dtype=np.float32).astype(np.float64)
+    want = torch.tensor(v, dtype=torch.float32).to(getattr(torch, tdt)).double().numpy()
+    got = O.round_to_format(v, fmt)
+    assert np.array_equal(got, want, equal_nan=True)
+    assert got[1] == np.inf and got[2] == vmax     # the tie at the top rounds to even: up
+
+
+def test_round_non_finite_hand_cases():
+    # e4m3 has no infinity: overflow and infinite inputs saturate at +-448 (satfinite);
+    # tf32 keeps float32's exponent range, so infinities stay infinite
+    got = O.round_to_format([np.inf, -np.inf, np.nan, 1e6, -464.0, 463.0], "e4m3")
+    assert got[0] == 448.0 and got[1] == -448.0 and np.isnan(got[2])
+    assert list(got[3:]) == [448.0, -448.0, 448.0]
+    got = O.round_to_format([np.inf, -np.inf, np.nan, 0.0], "tf32")
+    assert got[0] == np.inf and got[1] == -np.inf and np.isnan(got[2]) and got[3] == 0.0
+    # the largest tf32 value, and a float32 value that rounds (ties away) past it
+    tmax = O.FORMATS["tf32"][2]
+    assert O.round_to_format([tmax], "tf32")[0] == tmax
+    assert O.round_to_format([np.ldexp(4095.0 / 2048.0, 127)], "tf32")[0] == np.inf
+
+
+def test_quantize_assembles_parts_separately():
+    # an infinite imaginary part must not leak into the real part of the operand
+    Y = np.array([[[complex(1.0, np.inf), complex(np.nan, 0.5), 0.25 + 0j]]], np.complex64)
+    Q, se = O.quantize(Y, "fp16")
+    assert se[0, 0] == 0                                  # peak not finite: scale 1
+    assert Q.real[0, 0, 0] == 1.0 and Q.imag[0, 0, 0] == np.inf
+    assert np.isnan(Q.real[0, 0, 1]) and Q.imag[0, 0, 1] == 0.5
+    D = O.dequantize(Q, se)
+    assert D.real[0, 0, 0] == 1.0 and D.imag[0, 0, 0] == np.inf
+
+
 def test_round_e4m3_matches_torch_cast_in_range():
     torch = pytest.importorskip("torch")
     v = _edge_values()
