@@ -190,6 +190,17 @@ def test_paper_scale_workload(pk, dtype):
     H = _run(pk, Y, bits, w.K, w.L, dtype)
     ref = O.estimate(Y, bits, w.K, w.L)
     assert O.nmse(H, ref) <= TOL[dtype]
+    snr = w.frame_snr()
+    for s in np.unique(snr):                     # each SNR of the sweep on its own
+        f = snr == s
+        assert O.nmse(H[f], ref[f]) <= TOL[dtype], s
+    if dtype == "fp32":
+        assert np.abs(H - ref).max() <= 1e-5 * np.abs(ref).max()
+    else:                                        # the accumulation, apart from rounding Y
+        refq = O.estimate_quantized(Y, bits, w.K, w.L, dtype)
+        assert O.nmse(H, refq) <= TOL_Q[dtype]
+        per_frame = [O.nmse(H[i], refq[i]) for i in range(w.F)]
+        assert max(per_frame) <= TOL_Q[dtype]
 
 
 def test_noise_free_recovery_closed_form(pk):
