@@ -202,7 +202,7 @@ def estimate_fmt(Y: torch.Tensor, fmt: "FmtPilot", K: int, L: int, out=None) -> 
     if N != fmt.N:
         raise ValueError("Y's N differs from the transform's")
     dev = Y.device
-    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    H = _out_or_new(out, (F, M, K, L), dev)
     with torch.cuda.device(dev):
         check(lib().pnce_estimate_fmt(fmt.ctx.handle, fmt.handle, Y.data_ptr(), F, M, N, K, L,
                                       H.data_ptr(), _stream(dev)), "pnce_estimate_fmt")
@@ -223,11 +223,13 @@ def estimate_grouped(pilot: "Pilot", descs_ptr: int, nreq: int, rows: int, kl_ma
     pnce_req_desc entries (_lib.ReqDesc) that the GPU can read (device or page-locked
     host memory); each request's Y and H buffers likewise.  Enqueues only."""
     dev = pilot.device
+    _check_workspace(workspace, dev, grouped_workspace_size(rows, pilot.N, kl_max, dtype))
     with torch.cuda.device(dev):
         s = _stream(dev) if stream is None else stream
         check(lib().pnce_estimate_grouped(pilot.ctx.handle, pilot.handle, descs_ptr, nreq, rows,
                                           kl_max, _dt(dtype), workspace.data_ptr(),
-                                          workspace.numel(), s), "pnce_estimate_grouped")
+                                          workspace.numel() * workspace.element_size(), s),
+              "pnce_estimate_grouped")
 
 
 def backward_workspace_size(F, M, N, K, L) -> int:
@@ -265,6 +267,43 @@ def _check_y(Y: torch.Tensor, pilot: Pilot | None = None):
     return Y.shape
 
 
+def _check_out(out, shape, device, what="out", dtype=torch.complex64):
+    """`out` if it is a contiguous `dtype` tensor of `shape` on `device`, else ValueError.
+
+    Output and workspace pointers go to the kernels unchecked, so a buffer that is too
+    small, strided, or on another device must be refused here, before any launch."""
+    if not isinstance(out, torch.Tensor):
+        raise ValueError(f"{what} must be a torch.Tensor")
+    if out.dtype != dtype or tuple(out.shape) != tuple(shape):
+        raise ValueError(f"{what} must be a {dtype} tensor of shape {tuple(shape)}, "
+                         f"got {out.dtype} {tuple(out.shape)}")
+    if out.device != device:
+        raise ValueError(f"{what} is on {out.device}, expected {device}")
+    if not out.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    return out
+
+
+def _out_or_new(out, shape, device, pin_memory=False):
+    if out is None:
+        if device.type == "cpu":
+            return torch.empty(shape, dtype=torch.complex64, pin_memory=pin_memory)
+        return torch.empty(shape, dtype=torch.complex64, device=device)
+    return _check_out(out, shape, device)
+
+
+def _check_workspace(ws, device, need, what="workspace"):
+    """A caller-supplied workspace: a contiguous tensor on `device` of >= need bytes."""
+    if ws is None:
+        return None
+    if not isinstance(ws, torch.Tensor) or ws.device != device or not ws.is_contiguous():
+        raise ValueError(f"{what} must be a contiguous tensor on {device}")
+    if ws.numel() * ws.element_size() < need:
+        raise ValueError(f"{what} holds {ws.numel() * ws.element_size()} bytes, "
+                         f"{need} needed")
+    return ws
+
+
 SHIFT_RULES = {"kl": 0, "spread": 1}
 
 
@@ -285,9 +324,10 @@ def estimate(Y: torch.Tensor, pilot: Pilot, K: int, L: int, dtype="fp32", out=No
             raise ValueError(f"rows hold {T} samples, expected cp_len + N = {cp_len + N}")
     dt = _dt(dtype)
     dev = Y.device
-    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    H = _out_or_new(out, (F, M, K, L), dev)
     need = workspace_size(F, M, N, K, L, dt)
-    ws = workspace if workspace is not None else _workspace(dev, need)
+    ws = _check_workspace(workspace, dev, need) if workspace is not None \
+        else _workspace(dev, need)
     nbytes = 0 if ws is None else ws.numel() * ws.element_size()
     with torch.cuda.device(dev):
         if cp_len == 0 and shift_rule == "kl":
@@ -324,12 +364,14 @@ def quantize(Y: torch.Tensor, dtype, workspace=None, want_power=False):
         raise ValueError("fp32 has no quantised operand")
     dev = Y.device
     need = workspace_size(F, M, N, 1, 1, dt)
-    ws = workspace if workspace is not None else torch.empty(need, dtype=torch.uint8, device=dev)
+    ws = _check_workspace(workspace, dev, need) if workspace is not None \
+        else torch.empty(need, dtype=torch.uint8, device=dev)
     exps = torch.empty(F * M, dtype=torch.int32, device=dev)
     power = torch.empty(F * M, dtype=torch.float64, device=dev) if want_power else None
     with torch.cuda.device(dev):
         check(lib().pnce_quantize(context(dev).handle, Y.data_ptr(), F, M, N, dt, ws.data_ptr(),
-                                  ws.numel(), exps.data_ptr(), _ptr(power), _stream(dev)),
+                                  ws.numel() * ws.element_size(), exps.data_ptr(), _ptr(power),
+                                  _stream(dev)),
               "pnce_quantize")
     pitch = (N + 63) // 64 * 64
     eb = {1: 4, 2: 2, 3: 2, 4: 1}[dt]
@@ -346,12 +388,14 @@ def quantize(Y: torch.Tensor, dtype, workspace=None, want_power=False):
 def correlate_quantized(workspace: torch.Tensor, pilot: Pilot, F, M, K, L, dtype, out=None):
     """Tensor-core correlation of an operand already produced by quantize()."""
     dt = _dt(dtype)
-    dev = workspace.device
+    dev = pilot.device
     N = pilot.N
-    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    _check_workspace(workspace, dev, workspace_size(F, M, N, K, L, dt))
+    H = _out_or_new(out, (F, M, K, L), dev)
     with torch.cuda.device(dev):
         check(lib().pnce_correlate_quantized(pilot.ctx.handle, pilot.handle, F, M, N, K, L, dt,
-                                             workspace.data_ptr(), workspace.numel(),
+                                             workspace.data_ptr(),
+                                             workspace.numel() * workspace.element_size(),
                                              H.data_ptr(), _stream(dev)),
               "pnce_correlate_quantized")
     return H
@@ -370,7 +414,7 @@ def estimate_real_pilot(Y: torch.Tensor, p: torch.Tensor, K: int, L: int, out=No
     if p.dtype != torch.float32 or p.shape != (N,) or not p.is_contiguous() or p.device != Y.device:
         raise ValueError("p must be a contiguous float32 tensor [N] on Y's device")
     dev = Y.device
-    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64, device=dev)
+    H = _out_or_new(out, (F, M, K, L), dev)
     with torch.cuda.device(dev):
         check(lib().pnce_estimate_real_pilot(context(dev).handle, p.data_ptr(),
                                              PILOT_MAPS[pilot_map], Y.data_ptr(), F, M, N, K, L,
@@ -386,9 +430,9 @@ def backward(p: torch.Tensor, Y: torch.Tensor, G: torch.Tensor, K: int, L: int,
     With pilot_map="tanh" the second output is the gradient with respect to theta.
     """
     F, M, N = _check_y(Y)
-    if G.dtype != torch.complex64 or tuple(G.shape) != (F, M, K, L) or not G.is_contiguous():
-        raise ValueError("G must be a contiguous complex64 tensor [F, M, K, L]")
     dev = Y.device
+    _check_out(G, (F, M, K, L), dev, what="G")
+    _check_out(p, (N,), dev, what="p", dtype=torch.float32)
     dY = torch.empty((F, M, N), dtype=torch.complex64, device=dev) if need_dY else None
     dp = torch.empty(N, dtype=torch.float32, device=dev) if need_dp else None
     need = backward_workspace_size(F, M, N, K, L) if need_dp else 0
@@ -396,7 +440,8 @@ def backward(p: torch.Tensor, Y: torch.Tensor, G: torch.Tensor, K: int, L: int,
     with torch.cuda.device(dev):
         check(lib().pnce_backward(context(dev).handle, p.data_ptr(), PILOT_MAPS[pilot_map],
                                   Y.data_ptr(), G.data_ptr(), F, M, N, K, L, _ptr(dY), _ptr(dp),
-                                  _ptr(ws), 0 if ws is None else ws.numel(), _stream(dev)),
+                                  _ptr(ws), 0 if ws is None else ws.numel() * ws.element_size(),
+                                  _stream(dev)),
               "pnce_backward")
     return dY, dp
 
@@ -414,14 +459,17 @@ def estimate_host(Y_host: torch.Tensor, pilot: Pilot, K: int, L: int, dtype="fp3
     F, M, N = Y_host.shape
     dt = _dt(dtype)
     dev = pilot.device
-    H = out if out is not None else torch.empty((F, M, K, L), dtype=torch.complex64,
-                                                pin_memory=Y_host.is_pinned())
+    if N != pilot.N:
+        raise ValueError(f"Y_host has N={N} samples but the pilot has N={pilot.N}")
+    H = _out_or_new(out, (F, M, K, L), torch.device("cpu"), pin_memory=Y_host.is_pinned())
     need = host_workspace_size(F, M, N, K, L, dt)
-    ws = workspace if workspace is not None else _workspace(dev, need, key="host")
+    ws = _check_workspace(workspace, dev, need) if workspace is not None \
+        else _workspace(dev, need, key="host")
     with torch.cuda.device(dev):
         s = _stream(dev)
         check(lib().pnce_estimate_host(pilot.ctx.handle, pilot.handle, Y_host.data_ptr(), F, M,
-                                       N, K, L, dt, _ptr(ws), 0 if ws is None else ws.numel(),
+                                       N, K, L, dt, _ptr(ws),
+                                       0 if ws is None else ws.numel() * ws.element_size(),
                                        H.data_ptr(), s), "pnce_estimate_host")
         torch.cuda.current_stream(dev).synchronize()
     return H

@@ -287,3 +287,30 @@ def test_long_sequence_staged_pilot(pk, dtype):
     H = _run(pk, Y, bits, K, L, dtype)
     refq = O.estimate_quantized(Y, bits, K, L, dtype)
     assert O.nmse(H, refq) <= TOL_Q[dtype]
+
+
+def test_bad_output_buffers_rejected(pk):
+    # a too-small, strided, host or wrong-dtype `out` is refused before any launch, and
+    # the buffer it names is left as it was
+    bits, _, Y = _case(7, 8, 2, 16, 1)
+    dev = torch.device("cuda", 0)
+    pilot = pk.Pilot(bits, device=dev)
+    Yd = torch.from_numpy(Y).to(dev)
+    small = torch.full((1, 8, 2, 15), SENT, dtype=torch.complex64, device=dev)
+    for out in [small,
+                torch.empty((1, 8, 2, 16), dtype=torch.complex64),             # host memory
+                torch.empty((1, 8, 16, 2), dtype=torch.complex64, device=dev).transpose(2, 3),
+                torch.empty((1, 8, 2, 16), dtype=torch.complex128, device=dev)]:
+        for dtype in ("fp32", "fp16"):
+            with pytest.raises(ValueError):
+                pk.estimate(Yd, pilot, 2, 16, dtype=dtype, out=out)
+    with pytest.raises(ValueError):                  # a workspace that is too small
+        pk.estimate(Yd, pilot, 2, 16, dtype="fp16",
+                    workspace=torch.empty(16, dtype=torch.uint8, device=dev))
+    p = torch.zeros(127, dtype=torch.float32, device=dev)
+    G = torch.zeros((1, 8, 2, 16), dtype=torch.complex64, device=dev)
+    with pytest.raises(ValueError):                  # the pilot of the adjoint is checked
+        pk.backward(p[:100], Yd, G, 2, 16)
+    torch.cuda.synchronize()
+    assert bool((small == SENT).all())
+    assert pk.get_status(dev) == 0

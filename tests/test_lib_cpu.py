@@ -127,3 +127,36 @@ def test_empty_and_degenerate_shapes_rejected_up_front(lib):
                                      dummy, None) == 1
     # the full-lag case K*L = N is admissible
     assert lib.pnce_workspace_size(1, 4, 127, 1, 127, 2) > 0
+
+
+def test_binding_refuses_bad_output_buffers_before_launch():
+    # output and workspace pointers go to the kernels unchecked, so the Python wrappers
+    # must refuse a buffer of the wrong shape, dtype, device or layout up front
+    import torch
+    import paper_2206_05506_gb300 as pk
+
+    cpu = torch.device("cpu")
+    shape = (2, 3, 4, 5)
+    good = torch.empty(shape, dtype=torch.complex64)
+    assert pk._check_out(good, shape, cpu) is good
+    bad = [torch.empty((2, 3, 4, 4), dtype=torch.complex64),           # too small
+           torch.empty((2, 3, 4, 6), dtype=torch.complex64),           # wrong shape
+           torch.empty(shape, dtype=torch.complex128),                 # wrong dtype
+           torch.empty(shape, dtype=torch.float32),
+           torch.empty((2, 3, 5, 4), dtype=torch.complex64).transpose(2, 3),  # strided
+           torch.empty(shape, dtype=torch.complex64, device="meta"),   # another device
+           "not a tensor"]
+    for b in bad:
+        with pytest.raises(ValueError):
+            pk._check_out(b, shape, cpu)
+    with pytest.raises(ValueError):                 # a host buffer where a GPU one is due
+        pk._check_out(good, shape, torch.device("cuda", 0))
+    with pytest.raises(ValueError):                 # a pilot of the wrong length
+        pk._check_out(torch.empty(7), (8,), cpu, what="p", dtype=torch.float32)
+    ws = torch.empty(100, dtype=torch.uint8)
+    assert pk._check_workspace(ws, cpu, 100) is ws
+    assert pk._check_workspace(torch.empty(25, dtype=torch.float32), cpu, 100) is not None
+    for b, need in [(ws, 101), (torch.empty(100, dtype=torch.uint8, device="meta"), 10),
+                    (torch.empty(200, dtype=torch.uint8)[::2], 10)]:
+        with pytest.raises(ValueError):
+            pk._check_workspace(b, cpu, need)
