@@ -54,14 +54,30 @@ typedef enum {
 
 /* Arithmetic of the correlation.  FP32_SIMT: exact FP32 on the CUDA cores.  The others
  * quantise Y (per antenna, power-of-two scale) and run on the tensor cores with FP32
- * accumulation; +-1 pilots are exact in every one of these formats. */
+ * accumulation; +-1 pilots are exact in every one of these formats (Sec. III-B uses FP16
+ * operands).  AUTO lets the library choose from the shape, see pnce_auto_dtype. */
 typedef enum {
     PNCE_FP32_SIMT = 0,
     PNCE_TF32 = 1,
     PNCE_FP16 = 2,
     PNCE_BF16 = 3,
-    PNCE_FP8E4M3 = 4
+    PNCE_FP8E4M3 = 4,
+    PNCE_AUTO = 5
 } pnce_dtype;
+
+/*
+ * The arithmetic PNCE_AUTO stands for at this shape: PNCE_FP32_SIMT when K*L <= 16, else
+ * PNCE_FP16 (the paper's tensor-core operand format, Sec. III-B).  With few lags the
+ * correlation is bound by reading Y once (8 bytes per sample), which the FP32 kernel does
+ * at about the rate of the quantiser pass that every tensor-core estimate starts with, so
+ * exact FP32 costs nothing there; with more lags the tensor cores win by far.  Host only;
+ * returns -1 for an invalid shape.  pnce_workspace_size, pnce_estimate, pnce_estimate_ex,
+ * pnce_host_workspace_size, pnce_estimate_host, pnce_grouped_workspace_size and
+ * pnce_estimate_grouped (with K*L = kl_max) accept PNCE_AUTO and resolve it by this rule;
+ * pnce_quantize, pnce_correlate_quantized and pnce_estimate_static, which name one
+ * tensor-core step or format, do not.
+ */
+int pnce_auto_dtype(int N, int K, int L);
 
 typedef struct pnce_handle pnce_handle;   /* per-device context: latched device status */
 typedef struct pnce_pilot pnce_pilot;     /* device-resident pilot bit table of one sequence */
@@ -223,7 +239,7 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
 /*
  * Tracing.  While enabled, the estimate entry points (pnce_estimate, pnce_estimate_ex,
  * pnce_quantize, pnce_correlate_quantized, pnce_estimate_grouped, pnce_estimate_fmt,
- * pnce_estimate_real_pilot, pnce_backward) record a CUDA event before and after every
+ * pnce_estimate_real_pilot, pnce_backward, pnce_estimate_static) record a CUDA event before and after every
  * quantiser / correlation / adjoint launch, on the stream it runs on (internal streams
  * included), up to 8192 launches.  Each such launch is also an NVTX range named
  * "pnce.<kind>" (always on; a no-op unless a profiler is attached).
@@ -297,8 +313,11 @@ pnce_status pnce_scatter_rows(const void* src_dev, long long src_pitch, const ui
  * to hand it.
  *  - Every device that loads the library keeps the array until the process exits.
  *  - Shapes whose operand does not fit (pnce_workspace_size(...) > PNCE_STATIC_SCRATCH_BYTES,
- *    e.g. more than about 2000 antennas at N = 4095 in fp16) return PNCE_EINVAL and launch
- *    nothing; FP32_SIMT needs no scratch and is rejected here too (use pnce_estimate).
+ *    i.e. 16*ceil(A/8) rows of ceil(N/64)*64 elements of the dtype's size, 256-byte
+ *    rounded, plus 4*A bytes of factors, for A = F*M antennas: about 4000 antennas at
+ *    N = 4095 in fp16 or bf16, 8000 in e4m3, 2000 in tf32) return PNCE_EINVAL and launch
+ *    nothing; FP32_SIMT needs no scratch and is rejected here too (use pnce_estimate), as
+ *    is PNCE_AUTO.
  *  - The first call on a device looks up the array's device address; make that first call
  *    before any stream capture.
  *  - All calls share the one array and it keeps the last call's contents (nothing in it

@@ -12,7 +12,7 @@ from .build import LIB_PATH
 
 PNCE_OK, PNCE_EINVAL, PNCE_EUNSUPPORTED, PNCE_ENOMEM, PNCE_ECUDA, PNCE_ETIMEOUT, PNCE_ESTATE = range(7)
 
-DTYPES = {"fp32": 0, "tf32": 1, "fp16": 2, "bf16": 3, "e4m3": 4}
+DTYPES = {"fp32": 0, "tf32": 1, "fp16": 2, "bf16": 3, "e4m3": 4, "auto": 5}
 
 
 class PnceError(RuntimeError):
@@ -39,6 +39,7 @@ class FrameOpts(C.Structure):
 
 _SIGS = {
     "pnce_version": (_i, []),
+    "pnce_auto_dtype": (_i, [_i, _i, _i]),
     "pnce_status_string": (C.c_char_p, [_i]),
     "pnce_create": (_i, [C.POINTER(_vp)]),
     "pnce_destroy": (_i, [_vp]),

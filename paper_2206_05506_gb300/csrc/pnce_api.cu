@@ -289,8 +289,14 @@ pnce_status pnce_pilot_destroy(pnce_pilot* p) {
     return PNCE_OK;
 }
 
+int pnce_auto_dtype(int N, int K, int L) {
+    if (!shape_ok(1, 1, N, K, L)) return -1;
+    return pnce::resolve_dtype(PNCE_AUTO, (long long)K * L);
+}
+
 size_t pnce_workspace_size(int F, int M, int N, int K, int L, int dtype) {
     if (!shape_ok(F, M, N, K, L)) return 0;
+    dtype = pnce::resolve_dtype(dtype, (long long)K * L);
     if (dtype == PNCE_FP32_SIMT) return 0;
     if (!is_tc(dtype)) return 0;
     return pnce::quant_layout((long long)F * M, N, dtype).total;
@@ -339,6 +345,7 @@ pnce_status pnce_estimate(pnce_handle* h, const pnce_pilot* pilot, const void* Y
     if (!h || !pilot || !Y_dev || !H_dev) return PNCE_EINVAL;
     if (!shape_ok(F, M, N, K, L)) return PNCE_EINVAL;
     if (!aligned16(Y_dev) || !aligned16(H_dev)) return PNCE_EINVAL;
+    dtype = pnce::resolve_dtype(dtype, (long long)K * L);
     if (dtype != PNCE_FP32_SIMT && !is_tc(dtype)) return PNCE_EINVAL;
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
@@ -387,6 +394,7 @@ pnce_status pnce_estimate_ex(pnce_handle* h, const pnce_pilot* pilot, const void
     if (!shape_ok(F, M, N, K, L)) return PNCE_EINVAL;
     if (opts->shift_rule == PNCE_SHIFT_SPREAD && L > N / K) return PNCE_EINVAL;
     if (!aligned16(Y_dev) || !aligned16(H_dev)) return PNCE_EINVAL;
+    dtype = pnce::resolve_dtype(dtype, (long long)K * L);
     if (dtype != PNCE_FP32_SIMT && !is_tc(dtype)) return PNCE_EINVAL;
     pnce_status st = check_device(h);
     if (st != PNCE_OK) return st;
@@ -507,6 +515,7 @@ HostLayout host_layout(int F, int M, int N, int K, int L, int dtype) {
 
 size_t pnce_host_workspace_size(int F, int M, int N, int K, int L, int dtype) {
     if (!shape_ok(F, M, N, K, L)) return 0;
+    dtype = pnce::resolve_dtype(dtype, (long long)K * L);
     if (dtype != PNCE_FP32_SIMT && !is_tc(dtype)) return 0;
     return host_layout(F, M, N, K, L, dtype).total;
 }
@@ -516,6 +525,7 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
                                size_t workspace_bytes, void* H_host, void* stream) {
     if (!h || !pilot || !Y_host || !H_host || !workspace_dev) return PNCE_EINVAL;
     if (!shape_ok(F, M, N, K, L)) return PNCE_EINVAL;
+    dtype = pnce::resolve_dtype(dtype, (long long)K * L);
     if (dtype != PNCE_FP32_SIMT && !is_tc(dtype)) return PNCE_EINVAL;
     if (!aligned16(workspace_dev)) return PNCE_EINVAL;
     const HostLayout lay = host_layout(F, M, N, K, L, dtype);
@@ -549,60 +559,79 @@ pnce_status pnce_estimate_host(pnce_handle* h, const pnce_pilot* pilot, const vo
 
     // the pipeline starts after the work already queued on the caller's stream
     if (cudaEventRecord(h->ev_start, user) != cudaSuccess) return PNCE_ECUDA;
-    for (cudaStream_t s : {h->s_h2d, h->s_comp, h->s_d2h})
-        if (cudaStreamWaitEvent(s, h->ev_start, 0) != cudaSuccess) return PNCE_ECUDA;
-
-    for (int f0 = 0, i = 0; f0 < F; f0 += lay.fc, ++i) {
-        const int b = i % kPnceHostSlots;
-        const int fc = (F - f0 < lay.fc) ? (F - f0) : lay.fc;
-        void* yd = ws + lay.y_off[b];
-        void* hd = ws + lay.h_off[b];
-        // copy-in: slot b is free once the kernels of its previous chunk have read it
-        if (i >= kPnceHostSlots && cudaStreamWaitEvent(h->s_h2d, h->ev_comp[b], 0) != cudaSuccess)
-            return PNCE_ECUDA;
-        if (cudaMemcpyAsync(yd, yh + (size_t)f0 * frame_y, (size_t)fc * frame_y,
-                            cudaMemcpyHostToDevice, h->s_h2d) != cudaSuccess ||
-            cudaEventRecord(h->ev_in[b], h->s_h2d) != cudaSuccess)
-            return PNCE_ECUDA;
-        // kernels: need the input, and H slot b drained by the copy-out of its previous chunk
-        if (cudaStreamWaitEvent(h->s_comp, h->ev_in[b], 0) != cudaSuccess) return PNCE_ECUDA;
-        if (i >= kPnceHostSlots && cudaStreamWaitEvent(h->s_comp, h->ev_out[b], 0) != cudaSuccess)
-            return PNCE_ECUDA;
-        const long long A = (long long)fc * M;
-        if (dtype == PNCE_FP32_SIMT) {
-            st = from_cuda(pnce::launch_simt_bits(pilot, static_cast<const float2*>(yd), A, N,
-                                                  K * L, static_cast<float2*>(hd), h->s_comp));
-        } else {
-            const pnce::QuantLayout ql = pnce::quant_layout(A, N, dtype);
-            void* q = ws + lay.q_off;
-            st = from_cuda(pnce::launch_quantize(static_cast<const float2*>(yd), A, N, dtype,
-                                                 pnce::ws_operand(q, ql), pnce::ws_factors(q, ql),
-                                                 nullptr, nullptr, h->s_comp));
-            if (st == PNCE_OK)
-                st = pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(q, ql),
-                                     pnce::ws_factors(q, ql), static_cast<float2*>(hd),
-                                     h->s_comp);
+    // Host-side fault injection for the test of the join below: PNCE_TEST_HOST_FAIL_CHUNK=i
+    // makes the call give up with PNCE_ECUDA when it reaches chunk i, as a failed launch
+    // or copy there would.
+    const char* fail_env = getenv("PNCE_TEST_HOST_FAIL_CHUNK");
+    const long long fail_at = fail_env ? atoll(fail_env) : -1;
+    auto run = [&]() -> pnce_status {
+        for (cudaStream_t s : {h->s_h2d, h->s_comp, h->s_d2h})
+            if (cudaStreamWaitEvent(s, h->ev_start, 0) != cudaSuccess) return PNCE_ECUDA;
+        for (int f0 = 0, i = 0; f0 < F; f0 += lay.fc, ++i) {
+            if (i == fail_at) return PNCE_ECUDA;
+            const int b = i % kPnceHostSlots;
+            const int fc = (F - f0 < lay.fc) ? (F - f0) : lay.fc;
+            void* yd = ws + lay.y_off[b];
+            void* hd = ws + lay.h_off[b];
+            // copy-in: slot b is free once the kernels of its previous chunk have read it
+            if (i >= kPnceHostSlots &&
+                cudaStreamWaitEvent(h->s_h2d, h->ev_comp[b], 0) != cudaSuccess)
+                return PNCE_ECUDA;
+            if (cudaMemcpyAsync(yd, yh + (size_t)f0 * frame_y, (size_t)fc * frame_y,
+                                cudaMemcpyHostToDevice, h->s_h2d) != cudaSuccess ||
+                cudaEventRecord(h->ev_in[b], h->s_h2d) != cudaSuccess)
+                return PNCE_ECUDA;
+            // kernels: need the input, and H slot b drained by the copy-out of its previous
+            // chunk
+            if (cudaStreamWaitEvent(h->s_comp, h->ev_in[b], 0) != cudaSuccess) return PNCE_ECUDA;
+            if (i >= kPnceHostSlots &&
+                cudaStreamWaitEvent(h->s_comp, h->ev_out[b], 0) != cudaSuccess)
+                return PNCE_ECUDA;
+            const long long A = (long long)fc * M;
+            pnce_status cst;
+            if (dtype == PNCE_FP32_SIMT) {
+                cst = from_cuda(pnce::launch_simt_bits(pilot, static_cast<const float2*>(yd), A,
+                                                       N, K * L, static_cast<float2*>(hd),
+                                                       h->s_comp));
+            } else {
+                const pnce::QuantLayout ql = pnce::quant_layout(A, N, dtype);
+                void* q = ws + lay.q_off;
+                cst = from_cuda(pnce::launch_quantize(static_cast<const float2*>(yd), A, N,
+                                                      dtype, pnce::ws_operand(q, ql),
+                                                      pnce::ws_factors(q, ql), nullptr, nullptr,
+                                                      h->s_comp));
+                if (cst == PNCE_OK)
+                    cst = pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(q, ql),
+                                          pnce::ws_factors(q, ql), static_cast<float2*>(hd),
+                                          h->s_comp);
+            }
+            if (cst != PNCE_OK) return cst;
+            if (cudaEventRecord(h->ev_comp[b], h->s_comp) != cudaSuccess) return PNCE_ECUDA;
+            // copy-out
+            if (cudaStreamWaitEvent(h->s_d2h, h->ev_comp[b], 0) != cudaSuccess)
+                return PNCE_ECUDA;
+            const cudaError_t ce =
+                h_mapped ? pnce::launch_copy_to_host(hd, h_mapped + (size_t)f0 * frame_h,
+                                                     (size_t)fc * frame_h, h->num_sms, h->s_d2h)
+                         : cudaMemcpyAsync(hh + (size_t)f0 * frame_h, hd, (size_t)fc * frame_h,
+                                           cudaMemcpyDeviceToHost, h->s_d2h);
+            if (ce != cudaSuccess || cudaEventRecord(h->ev_out[b], h->s_d2h) != cudaSuccess)
+                return PNCE_ECUDA;
         }
-        if (st != PNCE_OK) return st;
-        if (cudaEventRecord(h->ev_comp[b], h->s_comp) != cudaSuccess) return PNCE_ECUDA;
-        // copy-out
-        if (cudaStreamWaitEvent(h->s_d2h, h->ev_comp[b], 0) != cudaSuccess) return PNCE_ECUDA;
-        const cudaError_t ce =
-            h_mapped ? pnce::launch_copy_to_host(hd, h_mapped + (size_t)f0 * frame_h,
-                                                 (size_t)fc * frame_h, h->num_sms, h->s_d2h)
-                     : cudaMemcpyAsync(hh + (size_t)f0 * frame_h, hd, (size_t)fc * frame_h,
-                                       cudaMemcpyDeviceToHost, h->s_d2h);
-        if (ce != cudaSuccess || cudaEventRecord(h->ev_out[b], h->s_d2h) != cudaSuccess)
-            return PNCE_ECUDA;
-    }
-    // the caller's stream resumes when all three pipeline streams are done
+        return PNCE_OK;
+    };
+    st = run();
+    // The caller's stream resumes when all three pipeline streams are done -- after an
+    // error part way too, so that a caller who synchronises its stream and then frees or
+    // reuses the buffers never races with copies or kernels of earlier chunks still in
+    // flight on the handle's streams.
     cudaStream_t ss[3] = {h->s_h2d, h->s_comp, h->s_d2h};
     for (int k = 0; k < 3; ++k) {
         if (cudaEventRecord(h->ev_done[k], ss[k]) != cudaSuccess ||
             cudaStreamWaitEvent(user, h->ev_done[k], 0) != cudaSuccess)
-            return PNCE_ECUDA;
+            if (st == PNCE_OK) st = PNCE_ECUDA;
     }
-    return PNCE_OK;
+    return st;
 }
 
 }  // extern "C"

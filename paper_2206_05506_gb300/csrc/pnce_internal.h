@@ -41,6 +41,12 @@ struct pnce_handle {
 };
 
 namespace pnce {
+// PNCE_AUTO: exact FP32 on the CUDA cores up to this many lags, FP16 tensor cores above
+constexpr int kAutoSimtMaxLags = 16;
+inline int resolve_dtype(int dtype, long long KL) {
+    if (dtype != PNCE_AUTO) return dtype;
+    return KL <= kAutoSimtMaxLags ? (int)PNCE_FP32_SIMT : (int)PNCE_FP16;
+}
 constexpr int kTraceMax = 8192;
 enum TraceKind {
     TRACE_QUANTIZE = 0,

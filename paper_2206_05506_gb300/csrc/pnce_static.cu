@@ -2,8 +2,7 @@
 // operand and the per-antenna output factors) in a fixed device array that is part of the
 // library image, so the call itself never allocates.  Meant for callers that cannot call
 // cudaMalloc on their path: real-time receive pipelines that must not hit the allocator
-// (its latency is unbounded and it may synchronise the device), code that runs while a
-// CUDA graph is being captured (allocation is not capturable), and hosts that hand the
+// (its latency is unbounded and it may synchronise the device), and hosts that hand the
 // library a fixed memory budget with no allocator at all.
 #include <mutex>
 
@@ -62,10 +61,14 @@ extern "C" pnce_status pnce_estimate_static(pnce_handle* h, const pnce_pilot* pi
     // rewritten by the quantiser first, and the pad columns past N are never read
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const pnce::QuantLayout lay = pnce::quant_layout(A, N, dtype);
-    if (pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
-                              pnce::ws_operand(ws, lay), pnce::ws_factors(ws, lay), nullptr,
-                              nullptr, s) != cudaSuccess)
-        return PNCE_ECUDA;
+    {
+        pnce::TraceScope tr(h, s, pnce::TRACE_QUANTIZE);
+        if (pnce::launch_quantize(static_cast<const float2*>(Y_dev), A, N, dtype,
+                                  pnce::ws_operand(ws, lay), pnce::ws_factors(ws, lay), nullptr,
+                                  nullptr, s) != cudaSuccess)
+            return PNCE_ECUDA;
+    }
+    pnce::TraceScope tr(h, s, pnce::TRACE_CORRELATE);
     return pnce::launch_tc(h, pilot, A, N, K * L, dtype, pnce::ws_operand(ws, lay),
                            pnce::ws_factors(ws, lay), static_cast<float2*>(H_dev), s);
 }

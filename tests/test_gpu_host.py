@@ -51,3 +51,29 @@ def test_host_path_many_chunks(pk):
     pk.estimate_host(Yh, pilot, 4, 64, dtype="fp16", out=Hh)
     Hd = pk.estimate(Yh.to(dev), pilot, 4, 64, dtype="fp16").cpu()
     assert torch.equal(Hh, Hd)
+
+
+def test_failure_part_way_leaves_no_work_in_flight(pk, monkeypatch):
+    # a call that gives up at chunk 3 (a failure injected on the host, as a failed launch
+    # or copy there would) still makes the caller's stream wait for the three chunks it had
+    # enqueued: once that stream is synchronised, their results are complete in H and no
+    # copy is still writing to it
+    w = C.Workload("t", r=12, M=128, K=4, L=64, F=130, snr_db=(10.0,), seed=4)
+    bits, _, Y = C.make(w)
+    dev = torch.device("cuda", 0)
+    pilot = pk.Pilot(bits, device=dev)
+    Yh = torch.from_numpy(Y).pin_memory()
+    sentinel = complex(3.0, -3.0)
+    Hh = torch.full((130, 128, 4, 64), sentinel, dtype=torch.complex64).pin_memory()
+    monkeypatch.setenv("PNCE_TEST_HOST_FAIL_CHUNK", "3")
+    with pytest.raises(pk.PnceError):
+        pk.estimate_host(Yh, pilot, 4, 64, dtype="fp16", out=Hh)
+    torch.cuda.current_stream(dev).synchronize()
+    monkeypatch.delenv("PNCE_TEST_HOST_FAIL_CHUNK")
+    Hd = pk.estimate(Yh.to(dev), pilot, 4, 64, dtype="fp16").cpu()
+    done = [bool(torch.equal(Hh[f], Hd[f])) for f in range(130)]
+    untouched = [bool((Hh[f] == sentinel).all()) for f in range(130)]
+    n = sum(done)
+    assert n > 0 and n % 3 == 0 and all(done[:n])          # three whole chunks, in order
+    assert all(untouched[n:])                               # nothing after them
+    assert pk.get_status(dev) == 0
