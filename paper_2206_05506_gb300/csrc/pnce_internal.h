@@ -164,13 +164,21 @@ cudaError_t launch_simt_real(const float* p, bool tanh_map, const float2* Y, lon
 cudaError_t launch_quantize(const float2* Y, long long A, int N, int dtype, void* operand,
                             float* factors, int32_t* exps, double* power, cudaStream_t s,
                             int max_blocks = 0, long long y_stride = 0 /* 0: N */);
-// status: PNCE_OK, or PNCE_ECUDA / PNCE_EUNSUPPORTED
+// Serving batches: gather + quantise in one kernel (one block per batch row; a row's
+// source comes from its request descriptor dd[row_req[row]]), launched as a programmatic
+// dependent of the kernel before it.
+cudaError_t launch_quantize_grouped(const pnce_req_desc* dd, const int* row_req, int rows, int N,
+                                    int dtype, void* operand, float* factors, cudaStream_t s);
+// status: PNCE_OK, or PNCE_ECUDA / PNCE_EUNSUPPORTED.  pdl: launch as a programmatic
+// dependent of the kernel before it on the stream (the kernel's set-up -- barriers, TMEM,
+// the resident pilot operand -- then overlaps that kernel's tail; it waits for it before
+// touching the operand).
 pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
                       int KL, int dtype, const void* operand, const float* factors, float2* H,
-                      cudaStream_t s);
+                      cudaStream_t s, bool pdl = false);
 pnce_status launch_tc_ex(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
                          const LagMap& lags, int dtype, const void* operand,
-                         const float* factors, float2* H, cudaStream_t s);
+                         const float* factors, float2* H, cudaStream_t s, bool pdl = false);
 // the two pointers of a workspace laid out by quant_layout
 inline void* ws_operand(void* ws, const QuantLayout& l) {
     return static_cast<unsigned char*>(ws) + l.a_offset;

@@ -178,9 +178,122 @@ cudaError_t launch_dt(const float2* Y, long long A, int N, void* operand, float*
     return cudaGetLastError();
 }
 
+// Serving batches (pnce_estimate_grouped): the row gather and the quantiser in one pass.
+// Block a handles batch row a: the request that owns it (row_req, built by the grouped
+// prep kernel) names where the received row lives -- page-locked host memory or device
+// memory -- and the block reads it from there once (kept in shared memory when STAGE),
+// so the samples cross the host link once and no batch copy of Y exists.  Rows no request
+// covers, and the padding rows of the last 8-antenna group, get zero codes and factor 0.
+// Launched as a programmatic dependent of the prep kernel: it lets the correlation that
+// follows start its set-up at once, then waits for the row map.
+template <int DT, bool STAGE>
+__global__ void __launch_bounds__(THREADS)
+grouped_quantize_kernel(const pnce_req_desc* __restrict__ dd, const int* __restrict__ row_req,
+                        int rows, int N, int pitch, void* __restrict__ Q,
+                        float* __restrict__ out_scale, float invN) {
+    extern __shared__ float2 s_row[];
+    __shared__ float s_max[THREADS / 32];
+    __shared__ float s_scale;
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int tid = threadIdx.x;
+    const long long a = blockIdx.x;
+    const int b = a < rows ? row_req[a] : -1;
+    if (b < 0) {
+        const float z[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int n = 4 * tid; n < N; n += 4 * THREADS) {
+            const int valid = min(4, N - n);
+            store4<DT>(Q, pnce::operand_row(a, 0), pitch, n, z, valid);
+            store4<DT>(Q, pnce::operand_row(a, 1), pitch, n, z, valid);
+        }
+        if (a < rows && tid == 0) out_scale[a] = 0.f;
+        return;
+    }
+    const pnce_req_desc q = dd[b];
+    const float2* row = static_cast<const float2*>(q.Y) + (long long)(a - q.row_offset) * N;
+
+    float amax = 0.f;
+    for (int n = tid; n < N; n += THREADS) {
+        const float2 y = row[n];
+        if constexpr (STAGE) s_row[n] = y;
+        amax = fmaxf(amax, fmaxf(fabsf(y.x), fabsf(y.y)));
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    if ((tid & 31) == 0) s_max[tid >> 5] = amax;
+    __syncthreads();
+    if (tid == 0) {
+        float m = 0.f;
+        for (int w = 0; w < THREADS / 32; ++w) m = fmaxf(m, s_max[w]);
+        int se = 0;
+        if (Fmt<DT>::target != 0 && m > 0.f && isfinite(m)) {
+            int ex;
+            frexpf(m, &ex);
+            se = Fmt<DT>::target - ex;
+            se = se < -100 ? -100 : (se > 100 ? 100 : se);
+        }
+        s_scale = ldexpf(1.0f, se);
+        out_scale[a] = ldexpf(invN, -se);
+    }
+    __syncthreads();
+    const float sc = s_scale;
+    for (int n = 4 * tid; n < N; n += 4 * THREADS) {
+        const int valid = min(4, N - n);
+        float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i < valid) {
+                const float2 y = STAGE ? s_row[n + i] : row[n + i];
+                re[i] = y.x * sc;
+                im[i] = y.y * sc;
+            }
+        }
+        store4<DT>(Q, pnce::operand_row(a, 0), pitch, n, re, valid);
+        store4<DT>(Q, pnce::operand_row(a, 1), pitch, n, im, valid);
+    }
+}
+
+template <int DT>
+cudaError_t launch_grouped_dt(const pnce_req_desc* dd, const int* row_req, int rows, int N,
+                              void* operand, float* factors, cudaStream_t s) {
+    const float invN = (float)(1.0 / (double)N);
+    const size_t row_bytes = (size_t)N * sizeof(float2);
+    const bool stage = row_bytes <= (size_t)48 * 1024;      // no opt-in shared memory needed
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((rows + 7) / 8 * 8), 1, 1);   // padding rows included
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = stage ? row_bytes : 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    const int pitch = pnce::row_pitch(N);
+    return stage ? cudaLaunchKernelEx(&cfg, grouped_quantize_kernel<DT, true>, dd, row_req, rows,
+                                      N, pitch, operand, factors, invN)
+                 : cudaLaunchKernelEx(&cfg, grouped_quantize_kernel<DT, false>, dd, row_req,
+                                      rows, N, pitch, operand, factors, invN);
+}
+
 }  // namespace
 
 namespace pnce {
+
+cudaError_t launch_quantize_grouped(const pnce_req_desc* dd, const int* row_req, int rows, int N,
+                                    int dtype, void* operand, float* factors, cudaStream_t s) {
+    switch (dtype) {
+        case PNCE_FP16:
+            return launch_grouped_dt<PNCE_FP16>(dd, row_req, rows, N, operand, factors, s);
+        case PNCE_BF16:
+            return launch_grouped_dt<PNCE_BF16>(dd, row_req, rows, N, operand, factors, s);
+        case PNCE_TF32:
+            return launch_grouped_dt<PNCE_TF32>(dd, row_req, rows, N, operand, factors, s);
+        case PNCE_FP8E4M3:
+            return launch_grouped_dt<PNCE_FP8E4M3>(dd, row_req, rows, N, operand, factors, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 int elem_bytes(int dtype) {
     switch (dtype) {

@@ -61,24 +61,41 @@ __device__ __forceinline__ bool desc_ok(const pnce_req_desc& q, int rows, int kl
            q.L >= 1 && (long long)q.K * q.L <= kl_max && q.Y != nullptr && q.H != nullptr;
 }
 
-// row_req[r] = the request that owns batch row r (-1 already written for every row)
-__global__ void __launch_bounds__(THREADS)
-grouped_map_kernel(const pnce_req_desc* __restrict__ d, int nreq, int rows, int kl_max,
-                   int* __restrict__ row_req, int* err) {
-    for (int b = blockIdx.x; b < nreq; b += gridDim.x) {
-        const pnce_req_desc q = d[b];
+constexpr int PREP_THREADS = 1024;
+
+// One block: copies the descriptor table (device or page-locked host memory) into the
+// workspace, clears the row -> request map, then lets each valid request claim its rows.
+// A row claimed twice (overlapping row ranges) latches PNCE_EINVAL; the first claim keeps
+// it.  One kernel in place of a table copy, a memset and a map kernel: fewer graph nodes
+// on the latency path of a serving batch.
+__global__ void __launch_bounds__(PREP_THREADS)
+grouped_prep_kernel(const pnce_req_desc* __restrict__ src, int nreq, int rows, int kl_max,
+                    pnce_req_desc* __restrict__ dd, int* __restrict__ row_req, int* err) {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    for (int b = threadIdx.x; b < nreq; b += PREP_THREADS) dd[b] = src[b];
+    for (int r = threadIdx.x; r < rows; r += PREP_THREADS) row_req[r] = -1;
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int b = warp; b < nreq; b += PREP_THREADS / 32) {
+        const pnce_req_desc q = dd[b];
         if (q.M <= 0) continue;
         if (!desc_ok(q, rows, kl_max)) {
-            if (threadIdx.x == 0) atomicCAS(err, 0, (int)PNCE_EINVAL);
+            if (lane == 0) atomicCAS(err, 0, (int)PNCE_EINVAL);
             continue;
         }
-        for (int m = threadIdx.x; m < q.M; m += THREADS) row_req[q.row_offset + m] = b;
+        bool clash = false;
+        for (int m = lane; m < q.M; m += 32)
+            clash |= atomicCAS(&row_req[q.row_offset + m], -1, b) != -1;
+        if (__any_sync(0xffffffffu, clash) && lane == 0) atomicCAS(err, 0, (int)PNCE_EINVAL);
     }
 }
 
+// FP32 path: the rows move into the batch buffer first (the SIMT kernel reads rows at a
+// fixed pitch).  A programmatic dependent of the prep kernel.
 __global__ void __launch_bounds__(THREADS)
 grouped_gather_kernel(const pnce_req_desc* __restrict__ d, const int* __restrict__ row_req,
                       int N, float2* __restrict__ Yb) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int r = blockIdx.x;
     const int b = row_req[r];
     if (b < 0) return;
@@ -88,9 +105,12 @@ grouped_gather_kernel(const pnce_req_desc* __restrict__ d, const int* __restrict
     for (int n = threadIdx.x; n < N; n += THREADS) dst[n] = src[n];
 }
 
+// A programmatic dependent of the correlation: waits for it, then moves every row's first
+// K*L lags into its request's result.
 __global__ void __launch_bounds__(THREADS)
 grouped_scatter_kernel(const pnce_req_desc* __restrict__ d, const int* __restrict__ row_req,
                        int kl_max, const float2* __restrict__ Hb) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int r = blockIdx.x;
     const int b = row_req[r];
     if (b < 0) return;
@@ -99,6 +119,21 @@ grouped_scatter_kernel(const pnce_req_desc* __restrict__ d, const int* __restric
     const float2* src = Hb + (long long)r * kl_max;
     float2* dst = static_cast<float2*>(q.H) + (long long)(r - q.row_offset) * kl;
     for (int j = threadIdx.x; j < kl; j += THREADS) dst[j] = src[j];
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kern)(KArgs...), unsigned grid, unsigned block,
+                             cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 struct GroupedLayout {
@@ -110,7 +145,10 @@ GroupedLayout grouped_layout(int rows, int N, int kl_max, int dtype) {
     l.d_off = 0;                                   // device copy of up to `rows` descriptors
     l.m_off = pnce::round_up((size_t)rows * sizeof(pnce_req_desc), 256);   // row -> request
     l.y_off = l.m_off + pnce::round_up((size_t)rows * sizeof(int), 256);
-    l.h_off = l.y_off + pnce::round_up((size_t)rows * N * sizeof(float2), 256);
+    // the batch copy of Y exists only for the FP32 path (the quantiser reads the rows
+    // from the requests' buffers directly)
+    const size_t y_bytes = dtype == PNCE_FP32_SIMT ? (size_t)rows * N * sizeof(float2) : 0;
+    l.h_off = l.y_off + pnce::round_up(y_bytes, 256);
     l.q_off = l.h_off + pnce::round_up((size_t)rows * kl_max * sizeof(float2), 256);
     l.total = l.q_off;
     if (dtype != PNCE_FP32_SIMT) l.total += pnce::quant_layout(rows, N, dtype).total;
@@ -119,6 +157,7 @@ GroupedLayout grouped_layout(int rows, int N, int kl_max, int dtype) {
 
 bool grouped_shape_ok(int rows, int N, int kl_max, int dtype) {
     if (rows < 1 || N < 2 || kl_max < 1 || kl_max > N) return false;
+    dtype = pnce::resolve_dtype(dtype, kl_max);
     if ((long long)rows * N > (1LL << 36)) return false;
     return dtype == PNCE_FP32_SIMT || dtype == PNCE_TF32 || dtype == PNCE_FP16 ||
            dtype == PNCE_BF16 || dtype == PNCE_FP8E4M3;
@@ -145,7 +184,7 @@ extern "C" {
 
 size_t pnce_grouped_workspace_size(int rows, int N, int kl_max, int dtype) {
     if (!grouped_shape_ok(rows, N, kl_max, dtype)) return 0;
-    return grouped_layout(rows, N, kl_max, dtype).total;
+    return grouped_layout(rows, N, kl_max, pnce::resolve_dtype(dtype, kl_max)).total;
 }
 
 pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
@@ -155,6 +194,8 @@ pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
     if (!h || !pilot || !workspace_dev || nreq < 0 || (nreq > 0 && !descs)) return PNCE_EINVAL;
     if (!grouped_shape_ok(rows, pilot->N, kl_max, dtype) || nreq > rows) return PNCE_EINVAL;
     if ((uintptr_t)workspace_dev & 255u) return PNCE_EINVAL;
+    if ((uintptr_t)descs & 7u) return PNCE_EINVAL;
+    dtype = pnce::resolve_dtype(dtype, kl_max);
     const GroupedLayout lay = grouped_layout(rows, pilot->N, kl_max, dtype);
     if (workspace_bytes < lay.total) return PNCE_EINVAL;
     int dev = -1;
@@ -166,22 +207,20 @@ pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int N = pilot->N;
     unsigned char* ws = static_cast<unsigned char*>(workspace_dev);
-    float2* Yb = reinterpret_cast<float2*>(ws + lay.y_off);
     float2* Hb = reinterpret_cast<float2*>(ws + lay.h_off);
-    // the table comes over once (one copy; from page-locked host memory it is a graph
-    // node like any other), so that the blocks read their descriptors from device memory
     pnce_req_desc* dd = reinterpret_cast<pnce_req_desc*>(ws + lay.d_off);
-    if (cudaMemcpyAsync(dd, descs, sizeof(pnce_req_desc) * (size_t)nreq, cudaMemcpyDefault,
-                        s) != cudaSuccess)
-        return PNCE_ECUDA;
     int* row_req = reinterpret_cast<int*>(ws + lay.m_off);
-    if (cudaMemsetAsync(row_req, 0xff, sizeof(int) * (size_t)rows, s) != cudaSuccess)
-        return PNCE_ECUDA;
-    const int gm = nreq < 2 * h->num_sms ? nreq : 2 * h->num_sms;
-    grouped_map_kernel<<<gm, THREADS, 0, s>>>(dd, nreq, rows, kl_max, row_req, h->status_dev);
-    grouped_gather_kernel<<<rows, THREADS, 0, s>>>(dd, row_req, N, Yb);
+    // prep (table copy + row map), then every kernel as a programmatic dependent of the one
+    // before it: four graph nodes on the tensor-core path (prep, gather-quantise,
+    // correlation, scatter)
+    grouped_prep_kernel<<<1, PREP_THREADS, 0, s>>>(descs, nreq, rows, kl_max, dd, row_req,
+                                                   h->status_dev);
     if (cudaGetLastError() != cudaSuccess) return PNCE_ECUDA;
     if (dtype == PNCE_FP32_SIMT) {
+        float2* Yb = reinterpret_cast<float2*>(ws + lay.y_off);
+        if (launch_dependent(grouped_gather_kernel, (unsigned)rows, THREADS, s,
+                             (const pnce_req_desc*)dd, (const int*)row_req, N, Yb) != cudaSuccess)
+            return PNCE_ECUDA;
         pnce::TraceScope tr(h, s, pnce::TRACE_SIMT);
         if (pnce::launch_simt_bits(pilot, Yb, rows, N, kl_max, Hb, s) != cudaSuccess)
             return PNCE_ECUDA;
@@ -190,18 +229,21 @@ pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
         void* q = ws + lay.q_off;
         {
             pnce::TraceScope tr(h, s, pnce::TRACE_QUANTIZE);
-            if (pnce::launch_quantize(Yb, rows, N, dtype, pnce::ws_operand(q, ql),
-                                      pnce::ws_factors(q, ql), nullptr, nullptr, s) != cudaSuccess)
+            if (pnce::launch_quantize_grouped(dd, row_req, rows, N, dtype, pnce::ws_operand(q, ql),
+                                              pnce::ws_factors(q, ql), s) != cudaSuccess)
                 return PNCE_ECUDA;
         }
         pnce::TraceScope tr(h, s, pnce::TRACE_CORRELATE);
         const pnce_status st = pnce::launch_tc(h, pilot, rows, N, kl_max, dtype,
                                                pnce::ws_operand(q, ql), pnce::ws_factors(q, ql),
-                                               Hb, s);
+                                               Hb, s, /*pdl=*/!h->trace_on);
         if (st != PNCE_OK) return st;
     }
-    grouped_scatter_kernel<<<rows, THREADS, 0, s>>>(dd, row_req, kl_max, Hb);
-    return cudaGetLastError() == cudaSuccess ? PNCE_OK : PNCE_ECUDA;
+    return launch_dependent(grouped_scatter_kernel, (unsigned)rows, THREADS, s,
+                            (const pnce_req_desc*)dd, (const int*)row_req, kl_max,
+                            (const float2*)Hb) == cudaSuccess
+               ? PNCE_OK
+               : PNCE_ECUDA;
 }
 
 pnce_status pnce_gather_rows(const uint64_t* src_rows, int rows, int nelem, void* dst_dev,

@@ -461,6 +461,10 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     __syncthreads();
     fence_after();
     const uint32_t tmem = ctl->tmem_base;
+    // Launched as a programmatic dependent (serving batches), the set-up above overlapped
+    // the kernel before this one; the operand, factors and H are touched only after it has
+    // finished.  Without that launch attribute this returns at once.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == 0) {
         // ------------------------------------------------------------ TMA producer
@@ -581,8 +585,11 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
             if (!got) break;
             fence_after();
             unsigned long long* te = &ctl->tempty[acc];
+            // pacing spreads the stores over the next tile's products; a CTA's last tile
+            // has none to overlap, so its stores go out at once
+            const long long spacing = t + gridDim.x < prm.num_tiles ? prm.epi_spacing : 0;
             drain_accumulator(tmem + acc * ACC_COLS, q, lane, rb * (BM / 2), row_scale, H,
-                              prm.A, prm.lags.ldH, BN, col0, valid, prm.epi_spacing, [&] {
+                              prm.A, prm.lags.ldH, BN, col0, valid, spacing, [&] {
                                   fence_before();
                                   __syncwarp();
                                   if (lane == 0) mbar_arrive(te);
@@ -916,7 +923,7 @@ unsigned long long wait_limit_ns() {
 template <int DT>
 pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
                       const pnce::LagMap& lags, const void* operand, const float* factors,
-                      float2* H, cudaStream_t s) {
+                      float2* H, cudaStream_t s, bool pdl) {
     using F = TcFmt<DT>;
     auto enc = encode_fn();
     if (!enc) return PNCE_ECUDA;
@@ -1062,6 +1069,21 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return PNCE_ECUDA;
+    if (pdl) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)grid, 1, 1);
+        cfg.blockDim = dim3(THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        const cudaError_t le =
+            cudaLaunchKernelEx(&cfg, kern, map, pilot->ext_bits_dev, factors, H, prm);
+        return le == cudaSuccess ? PNCE_OK : PNCE_ECUDA;
+    }
     kern<<<(unsigned)grid, THREADS, smem, s>>>(map, pilot->ext_bits_dev, factors, H, prm);
     return cudaGetLastError() == cudaSuccess ? PNCE_OK : PNCE_ECUDA;
 }
@@ -1072,22 +1094,26 @@ namespace pnce {
 
 pnce_status launch_tc_ex(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N,
                          const LagMap& lm, int dtype, const void* operand, const float* factors,
-                         float2* H, cudaStream_t s) {
+                         float2* H, cudaStream_t s, bool pdl) {
     if (!(h->cc_major == 10 && h->cc_minor == 3)) return PNCE_EUNSUPPORTED;
     switch (dtype) {
-        case PNCE_FP16: return launch_dt<PNCE_FP16>(h, pilot, A, N, lm, operand, factors, H, s);
-        case PNCE_BF16: return launch_dt<PNCE_BF16>(h, pilot, A, N, lm, operand, factors, H, s);
+        case PNCE_FP16:
+            return launch_dt<PNCE_FP16>(h, pilot, A, N, lm, operand, factors, H, s, pdl);
+        case PNCE_BF16:
+            return launch_dt<PNCE_BF16>(h, pilot, A, N, lm, operand, factors, H, s, pdl);
         case PNCE_FP8E4M3:
-            return launch_dt<PNCE_FP8E4M3>(h, pilot, A, N, lm, operand, factors, H, s);
-        case PNCE_TF32: return launch_dt<PNCE_TF32>(h, pilot, A, N, lm, operand, factors, H, s);
+            return launch_dt<PNCE_FP8E4M3>(h, pilot, A, N, lm, operand, factors, H, s, pdl);
+        case PNCE_TF32:
+            return launch_dt<PNCE_TF32>(h, pilot, A, N, lm, operand, factors, H, s, pdl);
         default: return PNCE_EINVAL;
     }
 }
 
 pnce_status launch_tc(const pnce_handle* h, const pnce_pilot* pilot, long long A, int N, int KL,
                       int dtype, const void* operand, const float* factors, float2* H,
-                      cudaStream_t s) {
-    return launch_tc_ex(h, pilot, A, N, lagmap_contiguous(KL), dtype, operand, factors, H, s);
+                      cudaStream_t s, bool pdl) {
+    return launch_tc_ex(h, pilot, A, N, lagmap_contiguous(KL), dtype, operand, factors, H, s,
+                        pdl);
 }
 
 }  // namespace pnce

@@ -131,3 +131,61 @@ def test_grouped_graph_replay_follows_descriptors(pk):
         for M, K, L, Y, H in reqs:
             ref = pk.estimate(Y.cuda().view(1, M, N), pilot, K, L, dtype="fp16").reshape(M, K * L)
             assert torch.equal(H, ref.cpu())
+
+
+def test_grouped_overlapping_rows_latch_einval(pk):
+    # two requests whose row ranges overlap (rows 4..7 claimed twice) are a caller error:
+    # PNCE_EINVAL is latched; a third request elsewhere in the batch is unaffected
+    bits = mseq.mseq_bits(9, 1)
+    N = bits.size
+    dev = torch.device("cuda", 0)
+    pilot = pk.Pilot(bits, device=dev)
+    reqs = _requests(N, [(8, 2, 16), (8, 2, 16), (6, 1, 32)], 7, True)
+    buf, arr = _table(pk, 3)
+    for i, (M, K, L, Y, H) in enumerate(reqs):
+        arr[i].Y, arr[i].H, arr[i].M, arr[i].K, arr[i].L = Y.data_ptr(), H.data_ptr(), M, K, L
+    arr[0].row_offset, arr[1].row_offset, arr[2].row_offset = 0, 4, 20
+    for dtype in ("fp16", "fp32"):
+        ws = torch.empty(pk.grouped_workspace_size(64, N, 32, dtype), dtype=torch.uint8,
+                         device=dev)
+        pk.estimate_grouped(pilot, buf.data_ptr(), 3, 64, 32, dtype, ws)
+        torch.cuda.synchronize()
+        assert pk.get_status(dev) == 1             # PNCE_EINVAL latched
+        M, K, L, Y, H = reqs[2]
+        ref = pk.estimate(Y.cuda().view(1, M, N), pilot, K, L, dtype=dtype).reshape(M, K * L)
+        if dtype == "fp32":
+            a, b = H.numpy(), ref.cpu().numpy()
+            assert np.sum(np.abs(a - b) ** 2) <= 1e-12 * np.sum(np.abs(b) ** 2)
+        else:
+            assert torch.equal(H, ref.cpu())
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_grouped_auto_dtype(pk, host):
+    # PNCE_AUTO resolves on kl_max: the FP32 path at <= 16 lags, fp16 tensor cores above
+    bits = mseq.mseq_bits(10, 2)
+    N = bits.size
+    dev = torch.device("cuda", 0)
+    pilot = pk.Pilot(bits, device=dev)
+    for kl_max, want in ((16, "fp32"), (64, "fp16")):
+        assert pk.lib().pnce_auto_dtype(N, 1, kl_max) == pk.DTYPES[want]
+        assert pk.grouped_workspace_size(128, N, kl_max, "auto") == \
+            pk.grouped_workspace_size(128, N, kl_max, want)
+        outs = []
+        for dtype in ("auto", want):
+            reqs = _requests(N, [(40, 2, kl_max // 2), (17, 1, kl_max)], 3, host)
+            buf, arr = _table(pk, 2)
+            off = 0
+            for i, (M, K, L, Y, H) in enumerate(reqs):
+                arr[i].Y, arr[i].H, arr[i].M, arr[i].K, arr[i].L = \
+                    Y.data_ptr(), H.data_ptr(), M, K, L
+                arr[i].row_offset = off
+                off += M
+            ws = torch.empty(pk.grouped_workspace_size(128, N, kl_max, dtype), dtype=torch.uint8,
+                             device=dev)
+            pk.estimate_grouped(pilot, buf.data_ptr(), 2, 128, kl_max, dtype, ws)
+            torch.cuda.synchronize()
+            assert pk.get_status(dev) == 0
+            outs.append([H.cpu() for *_, H in reqs])
+        for a, b in zip(*outs):
+            assert torch.equal(a, b)

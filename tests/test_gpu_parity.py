@@ -314,3 +314,20 @@ def test_bad_output_buffers_rejected(pk):
     torch.cuda.synchronize()
     assert bool((small == SENT).all())
     assert pk.get_status(dev) == 0
+
+
+def test_auto_dtype_follows_its_rule(pk):
+    # dtype "auto": the same bits as the FP32 path at <= 16 lags and as fp16 above
+    dev = torch.device("cuda", 0)
+    for shape in [(10, 9, 2, 8, 2), (10, 9, 1, 16, 2), (10, 9, 1, 17, 2), (10, 9, 8, 64, 2)]:
+        r, M, K, L, F = shape
+        bits, _, Y = _case(*shape, seed=3)
+        want = "fp32" if K * L <= 16 else "fp16"
+        Yd = torch.from_numpy(Y).to(dev)
+        pilot = pk.Pilot(bits, device=dev)
+        Ha = pk.estimate(Yd, pilot, K, L, dtype="auto")
+        Hw = pk.estimate(Yd, pilot, K, L, dtype=want)
+        assert torch.equal(Ha, Hw), shape
+        Hh = pk.estimate_host(torch.from_numpy(Y).pin_memory(), pilot, K, L, dtype="auto")
+        assert torch.equal(Hh, Hw.cpu()), shape
+    assert pk.get_status(dev) == 0

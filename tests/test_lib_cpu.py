@@ -160,3 +160,24 @@ def test_binding_refuses_bad_output_buffers_before_launch():
                     (torch.empty(200, dtype=torch.uint8)[::2], 10)]:
         with pytest.raises(ValueError):
             pk._check_workspace(b, cpu, need)
+
+
+def test_auto_dtype_rule(lib):
+    # PNCE_AUTO: exact FP32 on the CUDA cores up to 16 lags, fp16 tensor cores above
+    assert lib.pnce_auto_dtype(127, 1, 1) == 0
+    assert lib.pnce_auto_dtype(127, 2, 8) == 0
+    assert lib.pnce_auto_dtype(127, 1, 17) == 2
+    assert lib.pnce_auto_dtype(4095, 16, 128) == 2
+    assert lib.pnce_auto_dtype(127, 2, 64) == -1            # K*L > N: invalid shape
+    assert lib.pnce_auto_dtype(1, 1, 1) == -1
+    for F, M, N, K, L in [(3, 5, 1023, 2, 8), (3, 5, 1023, 8, 64), (1, 130, 4095, 16, 128)]:
+        want = lib.pnce_auto_dtype(N, K, L)
+        assert lib.pnce_workspace_size(F, M, N, K, L, 5) == lib.pnce_workspace_size(F, M, N, K, L, want)
+        assert lib.pnce_host_workspace_size(F, M, N, K, L, 5) == \
+            lib.pnce_host_workspace_size(F, M, N, K, L, want)
+    assert lib.pnce_grouped_workspace_size(64, 1023, 16, 5) == lib.pnce_grouped_workspace_size(64, 1023, 16, 0)
+    assert lib.pnce_grouped_workspace_size(64, 1023, 64, 5) == lib.pnce_grouped_workspace_size(64, 1023, 64, 2)
+    # the entry points that name one tensor-core step or format do not take it
+    dummy = C.c_void_p(256)
+    assert lib.pnce_quantize(dummy, dummy, 1, 8, 127, 5, dummy, 1 << 20, None, None, None) == 1
+    assert lib.pnce_estimate_static(dummy, dummy, dummy, 1, 8, 127, 2, 16, 5, dummy, None) == 1
