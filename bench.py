@@ -180,6 +180,26 @@ def _nmse(est, ref) -> float:
     return float(np.sum(np.abs(est - ref) ** 2) / np.sum(np.abs(ref) ** 2))
 
 
+def nmse_stats(est, ref, frame_snr, chunk: int = 32) -> dict:
+    """NMSE of est against the oracle's ref (both [F, ...]) over all frames, per SNR of the
+    sweep (frame f at frame_snr[f]) and the worst frame."""
+    est = np.asarray(est)
+    nf = ref.shape[0]
+    num = np.empty(nf)
+    den = np.empty(nf)
+    for f0 in range(0, nf, chunk):
+        e = est[f0:f0 + chunk].astype(np.complex128)
+        r = np.asarray(ref[f0:f0 + chunk]).astype(np.complex128)
+        ax = tuple(range(1, e.ndim))
+        num[f0:f0 + chunk] = (np.abs(e - r) ** 2).sum(axis=ax)
+        den[f0:f0 + chunk] = (np.abs(r) ** 2).sum(axis=ax)
+    snr = np.asarray(frame_snr)[:nf]
+    return {"nmse": float(num.sum() / den.sum()),
+            "nmse_by_snr_db": {f"{s:g}": float(num[snr == s].sum() / den[snr == s].sum())
+                               for s in np.unique(snr)},
+            "nmse_worst_frame": float(np.max(num / den)), "frames": int(nf)}
+
+
 # Received blocks of the serving trace: 32 per (M, N) shape, 471 MB in all (3.6x L2), handed
 # to the requests of each shape in turn, so that a request's block was last read about 512
 # requests (~470 MB of other blocks) earlier and comes over the host link, not from L2.
@@ -206,13 +226,23 @@ def oracle_references() -> dict:
             full[(M, N, slot)] = O.estimate(Yp[[slot]], bits, 1, N)[0, :, 0, :]
     w = C.SMALL
     bits, _, Y = C.make(w)
-    return {"serving": full, "small": O.estimate(Y, bits, w.K, w.L)}
+    ps = C.PAPER_SCALE
+    pbits, _, pY = C.make(ps)
+    return {"serving": full, "small": O.estimate(Y, bits, w.K, w.L),
+            "paper_scale": O.estimate(pY, pbits, ps.K, ps.L)}
 
 
-def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None):
+SWEEP_RATES_HZ = (10000.0, 20000.0, 40000.0, 80000.0, 160000.0)
+
+
+def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
+                sweep_rates=SWEEP_RATES_HZ, sweep_seconds: float = 2.0):
     """Poisson request stream (uneven M, N, K, L) through the continuous-batching server,
     tensor cores (fp16) and the plain FP32 SIMT path on the same trace.  refs: the oracle's
-    results per payload (from oracle_references) for the spot check, or None."""
+    results per payload (from oracle_references) for the spot check, or None.  Then, per
+    path, an arrival-rate sweep (shorter traces): p50 / p99 latency and delivered frames/s
+    at each offered rate, and the knee -- the highest offered rate still delivered (>= 95 %)
+    with p99 within 4x of the lowest rate's."""
     import torch
 
     from paper_2206_05506_gb300 import serve
@@ -220,39 +250,49 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None):
 
     pool = serving_payloads()
     pinned = {k: torch.from_numpy(v).pin_memory() for k, v in pool.items()}
-    specs = S.poisson_trace(rate_hz, seconds, seed=0, payload_slots=SERVING_SLOTS)
-    turn = {}
-    for sp in specs:                           # each shape's blocks in turn (see SERVING_SLOTS)
-        sp.slot = turn.get((sp.M, sp.N), 0)
-        turn[(sp.M, sp.N)] = (sp.slot + 1) % SERVING_SLOTS
     ring_elems = 64 << 20                      # 512 MB of page-locked results, reused in turn
+
+    def trace(rate, secs, seed):
+        specs = S.poisson_trace(rate, secs, seed=seed, payload_slots=SERVING_SLOTS)
+        turn = {}
+        for sp in specs:                       # each shape's blocks in turn (see SERVING_SLOTS)
+            sp.slot = turn.get((sp.M, sp.N), 0)
+            turn[(sp.M, sp.N)] = (sp.slot + 1) % SERVING_SLOTS
+        return specs
+
+    specs = trace(rate_hz, seconds, 0)
     ring = torch.zeros(ring_elems, dtype=torch.complex64, pin_memory=True)
     # spot check: every 100th request keeps its result in a buffer of its own
     checked = [sp for sp in specs if sp.rid % 100 == 0]
     check_buf = torch.zeros(max(1, sum(sp.M * sp.K * sp.L for sp in checked)),
                             dtype=torch.complex64, pin_memory=True)
-    res = {"rate_hz": rate_hz, "seconds": seconds, "requests": len(specs)}
-    for dtype, name in (("fp16", "fp16_tensor_core"), ("fp32", "fp32_simt")):
-        eng = serve.GpuEngine(S.pilot_bits, device=dev, dtype=dtype, slots=4)
-        eng.prepare([255, 511, 1023, 2047])
+
+    def requests(specs, spot):
         reqs, off, coff = [], 0, 0
         for sp in specs:
             n = sp.M * sp.K * sp.L
             y = pinned[(sp.M, sp.N)]
-            if sp.rid % 100 == 0:
-                h_addr = check_buf.data_ptr() + coff * 8
-                r = serve.Request(sp.rid, sp.t_arrival, sp.M, sp.N, sp.K, sp.L,
-                                  y.data_ptr() + sp.slot * sp.M * sp.N * 8, h_addr)
+            y_addr = y.data_ptr() + sp.slot * sp.M * sp.N * 8
+            if spot and sp.rid % 100 == 0:
+                r = serve.Request(sp.rid, sp.t_arrival, sp.M, sp.N, sp.K, sp.L, y_addr,
+                                  check_buf.data_ptr() + coff * 8)
                 r.coff = coff
                 coff += n
             else:
                 if off + n > ring_elems:
                     off = 0
-                r = serve.Request(sp.rid, sp.t_arrival, sp.M, sp.N, sp.K, sp.L,
-                                  y.data_ptr() + sp.slot * sp.M * sp.N * 8,
+                r = serve.Request(sp.rid, sp.t_arrival, sp.M, sp.N, sp.K, sp.L, y_addr,
                                   ring.data_ptr() + off * 8)
                 off += n
             reqs.append(r)
+        return reqs
+
+    res = {"rate_hz": rate_hz, "seconds": seconds, "requests": len(specs)}
+    sweep_specs = {rate: trace(rate, sweep_seconds, 1 + i) for i, rate in enumerate(sweep_rates)}
+    for dtype, name in (("fp16", "fp16_tensor_core"), ("fp32", "fp32_simt")):
+        eng = serve.GpuEngine(S.pilot_bits, device=dev, dtype=dtype, slots=4)
+        eng.prepare([255, 511, 1023, 2047])
+        reqs = requests(specs, True)
         serve.Server(eng).run([serve.Request(-1, 0.0, r.M, r.N, r.K, r.L, r.y_addr, r.h_addr)
                                for r in reqs[:200]])            # warm the path
         srv = serve.Server(eng, mem_cap_bytes=40e9)
@@ -269,8 +309,88 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None):
         st["spot_check"] = {"requests": len(errs), "share": len(errs) / max(1, len(reqs)),
                             "nmse_max": float(max(errs)) if errs else None,
                             "nmse_median": float(np.median(errs)) if errs else None}
+        sweep = []
+        for rate in sweep_rates:
+            sst = serve.Server(eng, mem_cap_bytes=40e9).run(requests(sweep_specs[rate], False))
+            sweep.append({"offered_hz": rate, "delivered_frames_per_s": sst["frames_per_s"],
+                          "p50_ms": sst["p50_ms"], "p99_ms": sst["p99_ms"],
+                          "max_ms": sst["max_ms"], "mean_batch_rows": sst["mean_batch_rows"],
+                          "failed": sst["failed"]})
+        base_p99 = sweep[0]["p99_ms"] if sweep else None
+        knee = None
+        for row in sweep:
+            if row["delivered_frames_per_s"] >= 0.95 * row["offered_hz"] and \
+                    row["p99_ms"] <= 4.0 * base_p99:
+                knee = row["offered_hz"]
+        st["rate_sweep"] = {"seconds_per_rate": sweep_seconds, "rows": sweep,
+                            "knee_offered_hz": knee}
         res[name] = st
+        del eng
+        torch.cuda.empty_cache()
     return res
+
+
+def run_paper_scale(dev, ref=None, reps: int = 50):
+    """The paper-scale workload (M = 64, N = 1023, K = 8, L = 64, 128 frames, SNR 0/10/20
+    dB): the plain FP32 SIMT path against the TF32 tensor-core path (and fp16), each with
+    its step time, throughput, the roofline fraction of its correlation kernel and, given
+    the oracle's estimate `ref`, its NMSE overall and per SNR."""
+    import torch
+
+    import paper_2206_05506_gb300 as pk
+
+    w = C.PAPER_SCALE
+    bits, _, Y = C.make(w)
+    Yd = torch.from_numpy(Y).to(dev)
+    pilot = pk.Pilot(bits, device=dev)
+    H = torch.empty((w.F, w.M, w.K, w.L), dtype=torch.complex64, device=dev)
+    peaks, peak_src = load_peaks()
+    taps = w.F * w.M * w.K * w.L
+    flops = 4.0 * w.F * w.M * w.N * w.K * w.L
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": w.name}
+    for dt in ("fp32", "tf32", "fp16"):
+        ws = (torch.empty(pk.workspace_size(w.F, w.M, w.N, w.K, w.L, dt), dtype=torch.uint8,
+                          device=dev) if dt != "fp32" else None)
+        for _ in range(5):
+            pk.estimate(Yd, pilot, w.K, w.L, dtype=dt, out=H, workspace=ws)
+        torch.cuda.synchronize()
+        pk.trace_enable(True, dev)
+        pk.trace_read(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            pk.estimate(Yd, pilot, w.K, w.L, dtype=dt, out=H, workspace=ws)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tr = pk.trace_read(dev)
+        pk.trace_enable(False, dev)
+        ms = e0.elapsed_time(e1) / reps
+        kind = "simt" if dt == "fp32" else "correlate"
+        kern_ms = float(np.median([t for k, t in tr if k == kind]))
+        q_ms = [t for k, t in tr if k == "quantize"]
+        achieved = flops / (kern_ms / 1e3) / 1e12
+        if dt == "fp32":
+            peak = sms * 128 * 2 * 2070.0 * 1e6 / 1e12
+            roof = {"bound": "alu", "kernel": "simt_corr_kernel", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": f"{sms} SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
+        else:
+            peak = peaks["bf16_tflops"] * DTYPE_RATIO[dt]
+            roof = {"bound": "tensor", "kernel": "tc_corr_kernel", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "peak_source": f"{peak_src} burst bf16 x {DTYPE_RATIO[dt]}"}
+        row = {"ms_per_step": ms, "value": taps / (ms / 1e3), "unit": "taps/s",
+               "kernel_ms": kern_ms,
+               "quantize_ms": float(np.median(q_ms)) if q_ms else 0.0, "roofline": roof}
+        if ref is not None:
+            row.update(nmse_stats(H.cpu().numpy(), ref, w.frame_snr()))
+        out[dt] = row
+        del ws
+    assert pk.get_status(dev) == 0
+    return out
 
 
 def rank_first_frame(F: int, rank: int, world: int) -> int:
@@ -542,6 +662,10 @@ def main():
                     help="time the one-frame launch-latency case (1/0)")
     ap.add_argument("--other-dtypes", type=int, default=1,
                     help="also time the other arithmetics on the same batch (1/0)")
+    ap.add_argument("--paper-experiments", type=int, default=10,
+                    help="iterations per point of the Sec. IV experiments (0: skip)")
+    ap.add_argument("--paper-scale", type=int, default=1,
+                    help="time FP32 SIMT vs TF32 / fp16 on the paper-scale workload (1/0)")
     args = ap.parse_args()
 
     w = C.WORKLOADS[args.workload]
@@ -704,16 +828,19 @@ def main():
     single = world == 1
     cpu = None
     nmse = None
+    accuracy = None
     if not args.no_cpu and single:
         from oracle import pn_oracle as O
         nf, cdt, Href = cpu_oracle_sample(bits, Y_host, K, L)
         cpu = {"value": nf * M * K * L / cdt, "unit": "taps/s", "cores": host_cores(),
                "kind": "oracle",
                "sample": f"first {nf} of {F} frames, FP64 Toeplitz product (numpy BLAS)"}
-        nmse = O.nmse(H[:nf].cpu().numpy(), Href)
+        accuracy = nmse_stats(H[:nf].cpu().numpy(), Href, w.frame_snr())
+        nmse = accuracy["nmse"]
         refs = oracle_references()
     else:
         refs = {}
+        Href = None
 
     serving = (run_serving(dev, args.serving_seconds, refs=refs.get("serving"))
                if args.serving_seconds > 0 and single else None)
@@ -738,9 +865,19 @@ def main():
             torch.cuda.synchronize()
             ms_o = a0.elapsed_time(a1) / n_o
             others[odt] = {"ms_per_step": ms_o, "value": taps_per_step / (ms_o / 1e3)}
+            if Href is not None:           # the same frames the oracle estimated
+                others[odt].update(nmse_stats(H[:Href.shape[0]].cpu().numpy(), Href,
+                                              w.frame_snr()))
             del ows
         assert pk.get_status(dev) == 0
 
+    paper_scale = (run_paper_scale(dev, refs.get("paper_scale"))
+                   if args.paper_scale and single else None)
+    paper_exp = None
+    if args.paper_experiments > 0 and single:
+        import paper_experiments as PE
+        paper_exp = PE.run(pk, dev, "fp16", iters=args.paper_experiments)
+        paper_exp["claims"] = PE.claims(paper_exp)
     yard = (run_yardsticks(dev, bits, Y, pilot, K, L, taps_per_step)
             if args.yardsticks and single else None)
     layouts = (run_layouts(dev, pilot, Y, K, L, taps_per_step)
@@ -771,10 +908,13 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
         "nmse_vs_oracle": nmse,
+        "accuracy": accuracy,
         "cpu_baseline": cpu,
         "serving": serving,
         "small_case": small,
         "other_dtypes": others,
+        "paper_scale": paper_scale,
+        "paper_experiments": paper_exp,
         "differentiation": differentiation,
         "yardsticks": yard,
         "layouts": layouts,
