@@ -277,9 +277,10 @@ pnce_status pnce_trace_read(pnce_handle* h, int* kinds, float* ms, int max_entri
  * requests' row ranges must not overlap), and
  * gets back H (complex64 [M][K*L]) = the first K*L lags of those rows, with lag
  * j = k*L + l as in pnce_estimate.  Y and H may be device memory or page-locked host
- * memory (read and written by the GPU over the host link).  M = 0 marks an empty slot.  A
- * descriptor with row_offset + M > rows, K*L > kl_max or a NULL buffer is skipped and
- * latches PNCE_EINVAL (pnce_get_status).  Batch rows no request covers are estimated from
+ * memory (read and written by the GPU over the host link), 8-byte aligned.  M = 0 marks
+ * an empty slot.  A descriptor with row_offset + M > rows, K*L > kl_max, or a NULL or
+ * misaligned buffer is skipped and latches PNCE_EINVAL (pnce_get_status), as does a row
+ * claimed by two descriptors (which of the two then gets it is not defined).  Batch rows no request covers are estimated from
  * whatever the workspace holds and discarded.  workspace_dev: 256-byte aligned,
  * pnce_grouped_workspace_size(rows, N, kl_max, dtype) bytes (0 for invalid shapes).
  * Enqueues gather, quantiser (tensor-core dtypes), correlation and scatter kernels on

@@ -212,11 +212,41 @@ grouped_quantize_kernel(const pnce_req_desc* __restrict__ dd, const int* __restr
     const pnce_req_desc q = dd[b];
     const float2* row = static_cast<const float2*>(q.Y) + (long long)(a - q.row_offset) * N;
 
+    // The row crosses the host link (or comes from device memory) once.  Sample pairs are
+    // read as 16-byte loads from the first 16-byte boundary on (a row of odd N starts
+    // half-way into one every other row), four pairs per thread issued before any is used
+    // so that enough requests are in flight to cover the link's latency.
     float amax = 0.f;
-    for (int n = tid; n < N; n += THREADS) {
-        const float2 y = row[n];
-        if constexpr (STAGE) s_row[n] = y;
-        amax = fmaxf(amax, fmaxf(fabsf(y.x), fabsf(y.y)));
+    const int head = ((uintptr_t)row & 15u) ? 1 : 0;
+    const int npairs = (N - head) >> 1;
+    const float4* pairs = reinterpret_cast<const float4*>(row + head);
+    for (int i0 = tid; i0 < npairs; i0 += 4 * THREADS) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * THREADS;
+            v[u] = i < npairs ? pairs[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * THREADS;
+            if (i < npairs) {
+                if constexpr (STAGE) {
+                    s_row[head + 2 * i] = make_float2(v[u].x, v[u].y);
+                    s_row[head + 2 * i + 1] = make_float2(v[u].z, v[u].w);
+                }
+                amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v[u].x), fabsf(v[u].y)),
+                                         fmaxf(fabsf(v[u].z), fabsf(v[u].w))));
+            }
+        }
+    }
+    if (tid < 2) {                     // the unpaired sample at the head and / or the tail
+        const int n = tid == 0 ? (head ? 0 : -1) : ((N - head) & 1 ? N - 1 : -1);
+        if (n >= 0) {
+            const float2 y = row[n];
+            if constexpr (STAGE) s_row[n] = y;
+            amax = fmaxf(amax, fmaxf(fabsf(y.x), fabsf(y.y)));
+        }
     }
 #pragma unroll
     for (int o = 16; o; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));

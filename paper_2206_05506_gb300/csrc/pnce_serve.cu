@@ -58,7 +58,8 @@ copy_out_kernel(const float2* __restrict__ src, float2* dst, long long n) {
 // map built on the device.
 __device__ __forceinline__ bool desc_ok(const pnce_req_desc& q, int rows, int kl_max) {
     return q.M > 0 && q.row_offset >= 0 && (long long)q.row_offset + q.M <= rows && q.K >= 1 &&
-           q.L >= 1 && (long long)q.K * q.L <= kl_max && q.Y != nullptr && q.H != nullptr;
+           q.L >= 1 && (long long)q.K * q.L <= kl_max && q.Y != nullptr && q.H != nullptr &&
+           ((uintptr_t)q.Y & 7u) == 0 && ((uintptr_t)q.H & 7u) == 0;
 }
 
 constexpr int PREP_THREADS = 1024;
@@ -118,7 +119,30 @@ grouped_scatter_kernel(const pnce_req_desc* __restrict__ d, const int* __restric
     const int kl = q.K * q.L;
     const float2* src = Hb + (long long)r * kl_max;
     float2* dst = static_cast<float2*>(q.H) + (long long)(r - q.row_offset) * kl;
-    for (int j = threadIdx.x; j < kl; j += THREADS) dst[j] = src[j];
+    // 16-byte stores from the first 16-byte boundary of the destination on (its rows of
+    // odd K*L start half-way into one every other row), loads of up to four pairs issued
+    // before the stores
+    const int head = ((uintptr_t)dst & 15u) ? 1 : 0;
+    const int npairs = (kl - head) >> 1;
+    float4* dpairs = reinterpret_cast<float4*>(dst + head);
+    for (int i0 = threadIdx.x; i0 < npairs; i0 += 4 * THREADS) {
+        float4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * THREADS;
+            if (i < npairs) {
+                const float2 x0 = src[head + 2 * i], x1 = src[head + 2 * i + 1];
+                v[u] = make_float4(x0.x, x0.y, x1.x, x1.y);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * THREADS;
+            if (i < npairs) dpairs[i] = v[u];
+        }
+    }
+    if (threadIdx.x == 0 && head) dst[0] = src[0];
+    if (threadIdx.x == 1 && ((kl - head) & 1)) dst[kl - 1] = src[kl - 1];
 }
 
 template <typename... KArgs, typename... Args>

@@ -71,6 +71,7 @@ struct TcParams {
     int stages;             // pipeline depth (<= STAGES)
     int b_region;           // bytes of the pilot operand region
     int res_rows;           // resident pilot: 16-byte rows to generate (0 otherwise)
+    int ext_words;          // words of the wrapped pilot bit table
     int drop_first_arrive;  // test hook: the per-stage pilot generator withholds its first
                             // arrive, so the MMA issuer's bounded wait must run out
     unsigned long long wait_limit_ns;
@@ -378,7 +379,7 @@ __device__ __forceinline__ uint4 pilot_row(uint32_t x) {
 // Pilot operand: core matrix D, row r (byte offset 128 D + 16 r) holds the EPR pilot
 // values starting at sequence index s_start + G*D + r (mod N).  Rows idx = 8 D + r are
 // shared out over nthr threads (a multiple of 8), thread `tid` taking tid, tid+nthr, ...
-template <int DT>
+template <int DT, bool SMEM_EXT = false>
 __device__ __forceinline__ void gen_pilot_rows(unsigned char* dst, const uint32_t* __restrict__ ext,
                                                int N, long long s_start, int rows, int tid,
                                                int nthr) {
@@ -389,7 +390,14 @@ __device__ __forceinline__ void gen_pilot_rows(unsigned char* dst, const uint32_
     int pos = (int)(((w0 % N) + N) % N);
     const int step = (int)(((long long)F::G * (nthr >> 3)) % N);
     for (int idx = tid; idx < rows; idx += nthr) {
-        const uint32_t lo = __ldg(ext + (pos >> 5)), hi = __ldg(ext + (pos >> 5) + 1);
+        uint32_t lo, hi;
+        if constexpr (SMEM_EXT) {             // a copy of the table in shared memory
+            lo = ext[pos >> 5];
+            hi = ext[(pos >> 5) + 1];
+        } else {
+            lo = __ldg(ext + (pos >> 5));
+            hi = __ldg(ext + (pos >> 5) + 1);
+        }
         const uint64_t win = (((uint64_t)hi << 32) | lo) >> (pos & 31);
         const uint4 v = pilot_row<DT>((uint32_t)win);
         *reinterpret_cast<uint4*>(dst + (idx >> 3) * 128 + (idx & 7) * 16) = v;
@@ -443,11 +451,25 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     }
     if constexpr (RES) {
         // the CTA's lag block never changes (grid is a multiple of num_jt): build the
-        // pilot operand of all its K blocks once
+        // pilot operand of all its K blocks once.  The bit table is first copied into the
+        // (still unused) operand stages with one coalesced pass, so that the generator's
+        // reads are shared-memory hits instead of a chain of global-load latencies -- the
+        // difference matters for grids of a few tiles (serving batches), where the set-up
+        // is a large part of the kernel.
         long long j0;
         int col0, valid;
         pnce::lag_tile(prm.lags, BN, blockIdx.x % num_jt, j0, col0, valid);
-        gen_pilot_rows<DT>(sB, ext, prm.N, -j0 - BN + 1, prm.res_rows, threadIdx.x, THREADS);
+        if (prm.ext_words <= prm.stages * a_stage / 4) {
+            uint32_t* sx = reinterpret_cast<uint32_t*>(sA);
+            for (int i = threadIdx.x; i < prm.ext_words; i += THREADS) sx[i] = __ldg(ext + i);
+            __syncthreads();
+            gen_pilot_rows<DT, true>(sB, sx, prm.N, -j0 - BN + 1, prm.res_rows, threadIdx.x,
+                                     THREADS);
+        } else {
+            gen_pilot_rows<DT>(sB, ext, prm.N, -j0 - BN + 1, prm.res_rows, threadIdx.x, THREADS);
+        }
+        // orders these generic accesses to shared memory (the pilot operand written, the
+        // table copy in the stages read) before the tensor cores and TMA use it
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 2) {
@@ -960,6 +982,7 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     prm.num_kb = (N + F::BK - 1) / F::BK;
     prm.wait_limit_ns = wait_limit_ns();
     prm.err = h->status_dev;
+    prm.ext_words = pilot->ext_words;
 
     long long grid = h->num_sms;
     if (grid >= prm.num_jt) grid = grid / prm.num_jt * prm.num_jt;
