@@ -297,12 +297,15 @@ __device__ __forceinline__ void tmem_wait_ld() {
 // `spacing` SM cycles apart: a tile's stores (128 KB per CTA at BN = 256) issued in one
 // burst take the L1 data path from the tensor cores' operand reads for a while, spread
 // over the next tile's products they cost less (measured: ~4 % of the kernel in a burst).
+// Chunks [c_lo, c_hi) of the 64-column chunks are drained (the last tile of a CTA with one
+// or two tiles is split between the epilogue warps and the idle role warps).
 template <typename Release>
 __device__ __forceinline__ void drain_accumulator(uint32_t tacc, int q, int lane,
                                                   long long ant_base, const float* row_scale,
                                                   float2* __restrict__ H, long long A, int ldH,
                                                   int BN, int col0, int valid,
-                                                  long long spacing, Release release) {
+                                                  long long spacing, int c_lo, int c_hi,
+                                                  Release release) {
     const long long c0 = clock64();
     const int g = lane >> 2, u4 = lane & 3;
     long long ant[2];
@@ -313,17 +316,18 @@ __device__ __forceinline__ void drain_accumulator(uint32_t tacc, int q, int lane
         rs[h] = ant[h] < A ? __ldg(row_scale + ant[h]) : 0.f;
     }
     const int nch = BN / 64 + ((BN & 63) ? 1 : 0);     // chunks of 64 columns (BN % 32 == 0)
-    for (int c = 0; c < nch; ++c) {
-        if (c > 0 && spacing > 0) {
+    const int ce = c_hi < nch ? c_hi : nch;
+    for (int c = c_lo; c < ce; ++c) {
+        if (c > c_lo && spacing > 0) {
             // bounded: the target lies at most nch * spacing cycles after c0
-            while (clock64() - c0 < c * spacing) __nanosleep(128);
+            while (clock64() - c0 < (c - c_lo) * spacing) __nanosleep(128);
         }
         uint32_t v[2][32];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
             tmem_ld16x256b_x8(tacc + ((uint32_t)(32 * q + 16 * h) << 16) + 64u * c, v[h]);
         tmem_wait_ld();
-        if (c == nch - 1) release();
+        if (c == ce - 1) release();
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             if (ant[h] >= A) continue;
@@ -428,6 +432,9 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int BN = prm.BN, num_jt = prm.num_jt, num_st = prm.num_st;
+    // tiles t = blockIdx.x + i * gridDim.x of this CTA
+    const long long my_tiles =
+        blockIdx.x < prm.num_tiles ? (prm.num_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     constexpr int kps = KPS;                    // K blocks per stage (prm.kps)
     constexpr int a_stage = KPS * A_BOX;        // prm.a_stage
 
@@ -608,16 +615,48 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
             fence_after();
             unsigned long long* te = &ctl->tempty[acc];
             // pacing spreads the stores over the next tile's products; a CTA's last tile
-            // has none to overlap, so its stores go out at once
-            const long long spacing = t + gridDim.x < prm.num_tiles ? prm.epi_spacing : 0;
+            // has none to overlap, so its stores go out at once, and in a CTA of one or two
+            // tiles the idle role warps drain the second half of its columns
+            const bool last = t + gridDim.x >= prm.num_tiles;
+            const long long spacing = last ? 0 : prm.epi_spacing;
+            const int nch = (BN + 63) / 64;
+            const int c_hi = last && my_tiles <= 2 ? (nch + 1) / 2 : nch;
             drain_accumulator(tmem + acc * ACC_COLS, q, lane, rb * (BM / 2), row_scale, H,
-                              prm.A, prm.lags.ldH, BN, col0, valid, spacing, [&] {
+                              prm.A, prm.lags.ldH, BN, col0, valid, spacing, 0, c_hi, [&] {
                                   fence_before();
                                   __syncwarp();
                                   if (lane == 0) mbar_arrive(te);
                               });
             acc ^= 1u;
             if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    if (warp < 4 && my_tiles >= 1 && my_tiles <= 2) {
+        // Warps 0-3 have finished their roles (warps 0 and 2 only in lane 0) and drain the
+        // second half of the columns of the CTA's last tile, with the epilogue warp of the
+        // same TMEM lane quarter.  With one or two tiles per CTA the last tile is the first
+        // use of its accumulator barrier, so the wait below cannot be satisfied by an
+        // earlier phase.
+        __syncwarp();
+        const long long il = my_tiles - 1;
+        const long long t = blockIdx.x + il * gridDim.x;
+        const uint32_t acc = (uint32_t)(il & 1);
+        const int nch = (BN + 63) / 64;
+        const int c_lo = (nch + 1) / 2;
+        if (c_lo < nch) {
+            long long j0;
+            int col0, valid;
+            pnce::lag_tile(prm.lags, BN, t % num_jt, j0, col0, valid);
+            int got = 1;
+            if (lane == 0) got = wait_bar_sleepy(&ctl->tfull[acc], 0u, ctl, prm);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (got) {
+                fence_after();
+                drain_accumulator(tmem + acc * ACC_COLS, warp & 3, lane, (t / num_jt) * (BM / 2),
+                                  row_scale, H, prm.A, prm.lags.ldH, BN, col0, valid, 0, c_lo,
+                                  nch, [] {});
+            }
         }
     }
 
@@ -894,7 +933,8 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
             fence_after();
             unsigned long long* te = &ctl->tempty[acc];
             drain_accumulator(tmem + acc * ACC_COLS, q, lane, rb * (BM / 2), row_scale, H,
-                              prm.A, prm.lags.ldH, BN, col0, valid, prm.epi_spacing, [&] {
+                              prm.A, prm.lags.ldH, BN, col0, valid, prm.epi_spacing, 0,
+                              (BN + 63) / 64, [&] {
                                   fence_before();
                                   __syncwarp();
                                   if (lane == 0) {
@@ -1024,6 +1064,13 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
             STAGES, avail / (MAX_KPS * A_BOX + b_stage_bytes<DT>()));
         prm.b_region = prm.stages * b_stage_bytes<DT>();
         prm.res_rows = 0;
+    }
+    // A CTA with a single tile needs no deep pipeline; four stages keep its shared memory
+    // small enough to become resident beside the blocks of the kernel before it, so that
+    // a programmatic dependent launch overlaps its set-up with that kernel.
+    if ((prm.num_tiles + grid - 1) / grid <= 1 && prm.stages > 4) {
+        prm.stages = 4;
+        if (!res) prm.b_region = prm.stages * b_stage_bytes<DT>();
     }
     prm.a_stage = prm.kps * A_BOX;
     prm.num_st = (prm.num_kb + prm.kps - 1) / prm.kps;
