@@ -182,6 +182,142 @@ simt_corr_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ pr
     }
 }
 
+// The same tile with no block-wide barrier in its main loop: the pilot window of the whole
+// reduction is staged once per block (E[t] = pilot[(t - eoff) mod nmod] for t <
+// win_len(Nred), every chunk's window included), and every warp double-buffers its own RA
+// rows with cp.async and warp-level synchronisation only.  In the chunked kernel above,
+// the per-chunk __syncthreads kept warps waiting on the slowest one (ncu: barrier stalls
+// about a quarter of all stall cycles).  Used when the window fits (WIN_MAX entries).
+constexpr int WIN_MAX = 8192 + TJ + 8;
+
+template <int RA>
+struct WSmem {
+    float2 y[WARPS][2][RA][NC];
+};
+
+// entries of the whole window: the last chunk reads up to entry (nchunks - 1) * NC + ELEN - 1
+__host__ __device__ constexpr int win_len(int nred) { return (nred + NC - 1) / NC * NC + TJ + 8; }
+__host__ __device__ constexpr size_t win_bytes(int nred) {
+    return ((size_t)win_len(nred) + (size_t)win_len(nred) / 32 + 1) * sizeof(float);
+}
+
+template <int MODE, int RA>
+__global__ void __launch_bounds__(256, 2)
+simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ preal,
+                      const float2* __restrict__ Y, long long y_stride, long long A,
+                      int N /* reduction length */, const pnce::LagMap lags, int nmod,
+                      int num_jt, long long groups, float invN, float2* __restrict__ H) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WSmem<RA>& sm = *reinterpret_cast<WSmem<RA>*>(smem_raw);
+    float* E = reinterpret_cast<float*>(smem_raw + sizeof(WSmem<RA>));
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long bid = blockIdx.x;
+    long long j0;
+    int col0, valid;
+    pnce::lag_tile(lags, TJ, bid % num_jt, j0, col0, valid);
+    const long long g = bid / num_jt, gbase = A / groups, grem = A % groups;
+    const long long a0 = g * gbase + (g < grem ? g : grem);
+    const int rows = (int)(gbase + (g < grem ? 1 : 0));
+    const int nchunks = (N + NC - 1) / NC;
+    const long long eoff = j0 + TJ - 1;
+
+    {   // the whole pilot window, once
+        const int elen = win_len(N);
+        long long q0 = ((long long)tid - eoff) % nmod;
+        if (q0 < 0) q0 += nmod;
+        int q = (int)q0;
+        const int step = 256 % nmod;
+        for (int t = tid; t < elen; t += 256) {
+            E[epos(t)] = pilot_value<MODE>(bits, preal, q, nmod);
+            q += step;
+            if (q >= nmod) q -= nmod;
+        }
+    }
+    __syncthreads();
+    if (warp * RA >= rows) return;             // no block-wide barrier below
+
+    auto stage = [&](int c, int buf) {
+        const int n0 = c * NC;
+        for (int i = lane; i < RA * NC; i += 32) {
+            const int aa = i / NC, nn = i % NC;
+            const int r = warp * RA + aa;
+            const bool ok = (r < rows) && (n0 + nn < N);
+            const float2* src = ok ? (Y + (a0 + r) * y_stride + n0 + nn) : Y;
+            cp_async8(&sm.y[warp][buf][aa][nn], src, ok);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+
+    float2 acc[RA][RJ];
+#pragma unroll
+    for (int i = 0; i < RA; ++i)
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) acc[i][r] = make_float2(0.f, 0.f);
+    const int base = TJ - 1 - RJ * lane;
+
+    stage(0, 0);
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunks) {
+            stage(c + 1, buf ^ 1);
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        }
+        __syncwarp();
+        const int cb = c * NC + base;
+        float w[15];
+#pragma unroll
+        for (int i = 0; i < 15; ++i) w[i] = E[epos(cb - 7 + i)];
+
+#pragma unroll 2   // the sliding window's shifts become register renames
+        for (int s = 0; s < NC / 8; ++s) {
+            float nw[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) nw[i] = E[epos(cb + 8 * s + 8 + i)];
+#pragma unroll
+            for (int u2 = 0; u2 < 8; u2 += 2) {
+                float4 yy[RA];
+#pragma unroll
+                for (int i = 0; i < RA; ++i)
+                    yy[i] = *reinterpret_cast<const float4*>(&sm.y[warp][buf][i][8 * s + u2]);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int u = u2 + h;
+#pragma unroll
+                    for (int r = 0; r < RJ; ++r) {
+                        const float pv = w[u - r + 7];
+#pragma unroll
+                        for (int i = 0; i < RA; ++i) {
+                            const float yx = h ? yy[i].z : yy[i].x, yi = h ? yy[i].w : yy[i].y;
+                            acc[i][r] = __ffma2_rn(make_float2(pv, pv), make_float2(yx, yi),
+                                                   acc[i][r]);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 7; ++i) w[i] = w[i + 8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) w[7 + i] = nw[i];
+        }
+        __syncwarp();                          // buf is free for chunk c + 2
+    }
+
+#pragma unroll
+    for (int i = 0; i < RA; ++i) {
+        if (warp * RA + i >= rows) continue;
+        const long long a = a0 + warp * RA + i;
+        float2* hrow = H + a * lags.ldH + col0;
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) {
+            const int j = RJ * lane + r;
+            if (j < valid) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
+        }
+    }
+}
+
 // Few lags (K*L <= 32, lags contiguous): the block tile above would leave most lanes idle,
 // and at ~2 K*L flops per 8-byte sample the work is close to the HBM roofline.  One warp
 // per received row: lane l takes samples l, l+32, ... (coalesced 8-byte loads, read once)
@@ -265,6 +401,17 @@ cudaError_t launch_ra(const uint32_t* bits, const float* preal, const float2* Y,
                       int num_jt, long long groups, float2* H, cudaStream_t s) {
     const long long blocks = (long long)num_jt * groups;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
+    if (win_len(N) <= WIN_MAX) {
+        const size_t wsmem = sizeof(WSmem<RA>) + win_bytes(N);
+        cudaError_t e = cudaFuncSetAttribute(simt_corr_warp_kernel<MODE, RA>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)wsmem);
+        if (e != cudaSuccess) return e;
+        simt_corr_warp_kernel<MODE, RA><<<(unsigned)blocks, 256, wsmem, s>>>(
+            bits, preal, Y, y_stride, A, N, lags, nmod, num_jt, groups,
+            (float)(1.0 / (double)nmod), H);
+        return cudaGetLastError();
+    }
     const size_t smem = sizeof(Smem<RA>);
     cudaError_t e = cudaFuncSetAttribute(simt_corr_kernel<MODE, RA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
