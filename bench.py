@@ -647,6 +647,8 @@ def main():
     ap.add_argument("--workload", default=C.PRECISION.name, choices=sorted(C.WORKLOADS))
     ap.add_argument("--dtype", default="fp16", choices=["fp32", "tf32", "fp16", "bf16", "e4m3"])
     ap.add_argument("--frames", type=int, default=None, help="override frames per step")
+    ap.add_argument("--K", type=int, default=None, help="override the transmitters (K)")
+    ap.add_argument("--L", type=int, default=None, help="override the taps per transmitter (L)")
     ap.add_argument("--e2e-steps", type=int, default=16)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--ref-frames", type=int, default=8, help="frames per reference step")
@@ -669,9 +671,12 @@ def main():
     args = ap.parse_args()
 
     w = C.WORKLOADS[args.workload]
-    if args.frames:
-        w = C.Workload(w.name if args.frames == w.F else f"{w.name}_x{args.frames}", r=w.r,
-                       M=w.M, K=w.K, L=w.L, F=args.frames, snr_db=w.snr_db, seed=w.seed)
+    if args.frames or args.K or args.L:
+        F = args.frames or w.F
+        K = args.K or w.K
+        L = args.L or w.L
+        name = w.name if (F, K, L) == (w.F, w.K, w.L) else f"n{w.N}_m{w.M}_k{K}_l{L}_f{F}"
+        w = C.Workload(name, r=w.r, M=w.M, K=K, L=L, F=F, snr_db=w.snr_db, seed=w.seed)
     if args.impl == "reference":
         run_reference(args, w)
         return

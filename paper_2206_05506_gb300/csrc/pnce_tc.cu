@@ -670,237 +670,6 @@ tc_corr_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     }
 }
 
-// ---------------------------------------- lag-major variant (tiles of <= 128 lags)
-//
-// With the transmitters' cyclic shifts spread out (Eq. 8), a lag tile is one transmitter's
-// L lags; at L = 128 the kernel above would issue MMAs of N = 128, whose operand reads
-// (4 KB of received rows + 4 KB of pilot per 64 clocks) exceed the shared-memory data
-// path.  Here the roles swap: the pilot tile (128 lags x K, the same Hankel core-matrix
-// list, resident for all K blocks) is the A operand and 256 received operand rows
-// (128 antennas, one 32 KB TMA box per K block) are the B operand, so every MMA is again
-// M = 128 x N = 256 (4 KB + 8 KB per 128 clocks).  The accumulator then holds lags in its
-// TMEM lanes and operand rows in its columns: a 32x32b load gives each epilogue thread one
-// lag for 32 operand rows -- the real and imaginary parts of 16 antennas -- and a warp's
-// store writes 32 consecutive lags (256 bytes) of one antenna.
-
-constexpr int BR = 256;                   // operand rows per lag-major tile (the MMA's N)
-constexpr int Y_BOX = BR * 128;           // one TMA box of them: 256 rows x 128 B = 32 KB
-
-// 32 TMEM lanes x 32 columns: thread t receives lane (base + t), columns c .. c+31
-__device__ __forceinline__ void tmem_ld32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
-        "[%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
-          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
-          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
-          "=r"(v[31])
-        : "r"(taddr));
-}
-
-template <int DT>
-__global__ void __launch_bounds__(THREADS, 1)
-tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
-                   const float* __restrict__ row_scale, float2* __restrict__ H,
-                   const TcParams prm) {
-    using F = TcFmt<DT>;
-    constexpr int KSTEPS = 4;                  // MMAs per K block: 128 B of K, 32 B each
-    constexpr int TL = 128;                    // lags per tile (the MMA's M)
-    constexpr uint32_t LBO = 128u * F::TS, SBO = 128u * F::QS;
-    constexpr uint32_t KSTEP_P = 2u * 128u * F::TS;       // pilot bytes per MMA K step
-
-    extern __shared__ unsigned char smem_raw[];
-    unsigned char* base = reinterpret_cast<unsigned char*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const int nst = prm.stages;
-    unsigned char* sY = base;
-    unsigned char* sP = sY + nst * Y_BOX;
-    Ctl* ctl = reinterpret_cast<Ctl*>(sP + prm.b_region);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int num_jt = prm.num_jt, num_kb = prm.num_kb;
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < nst; ++s) {
-            mbar_init(&ctl->full_a[s], 1);
-            mbar_init(&ctl->empty[s], 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&ctl->tfull[b], 1);
-            mbar_init(&ctl->tempty[b], 4);
-        }
-        ctl->abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (warp == 0 && lane == 0) {
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
-                     : "memory");
-    }
-    {
-        // the CTA's lag block is fixed (the grid is a multiple of num_jt): its pilot operand
-        // for every K block, generated once from a shared-memory copy of the bit table
-        long long j0;
-        int col0, valid;
-        pnce::lag_tile(prm.lags, TL, blockIdx.x % num_jt, j0, col0, valid);
-        if (prm.ext_words <= nst * Y_BOX / 4) {
-            uint32_t* sx = reinterpret_cast<uint32_t*>(sY);
-            for (int i = threadIdx.x; i < prm.ext_words; i += THREADS) sx[i] = __ldg(ext + i);
-            __syncthreads();
-            gen_pilot_rows<DT, true>(sP, sx, prm.N, -j0 - TL + 1, prm.res_rows, threadIdx.x,
-                                     THREADS);
-        } else {
-            gen_pilot_rows<DT>(sP, ext, prm.N, -j0 - TL + 1, prm.res_rows, threadIdx.x, THREADS);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
-    if (warp == 2) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         su32(&ctl->tmem_base)),
-                     "r"(TMEM_COLS)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    fence_before();
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = ctl->tmem_base;
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-
-    if (warp == 0) {
-        // ------------------------------------------------------------ TMA producer
-        if (lane == 0) {
-            uint32_t stage = 0, phase = 0;
-            long long issued = 0;
-            bool ok = true;
-            for (long long t = blockIdx.x; t < prm.num_tiles && ok; t += gridDim.x) {
-                const int y = (int)(t / num_jt) * BR;
-                for (int kb = 0; kb < num_kb; ++kb) {
-                    if (!wait_bar(&ctl->empty[stage], phase ^ 1u, ctl, prm, true)) {
-                        ok = false;
-                        break;
-                    }
-                    mbar_arrive_tx(&ctl->full_a[stage], Y_BOX);
-                    tma_load_2d(sY + stage * Y_BOX, &tmap, kb * F::BK, y, &ctl->full_a[stage]);
-                    ++issued;
-                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
-                }
-            }
-            const long long first = issued > nst ? issued - nst : 0;
-            for (long long i = first; i < issued; ++i)
-                wait_bar(&ctl->full_a[i % nst], (uint32_t)((i / nst) & 1), ctl, prm, false);
-        }
-    } else if (warp == 2) {
-        // ------------------------------------------------------------- MMA issuer
-        if (lane == 0) {
-            const uint32_t idesc = (1u << 4) | F::AB | ((uint32_t)(BR >> 3) << 17) |
-                                   ((uint32_t)(BM >> 4) << 24);
-            const uint64_t pdesc0 = sdesc(su32(sP), LBO, SBO, 0u);      // A: pilot, Hankel list
-            const uint64_t ydesc0 = sdesc(su32(sY), 16u, 1024u, 2u);    // B: rows, 128B swizzle
-            uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
-            unsigned long long* last_bar = nullptr;
-            uint32_t last_par = 0;
-            bool ok = true;
-            for (long long t = blockIdx.x; t < prm.num_tiles && ok; t += gridDim.x) {
-                if (!wait_bar(&ctl->tempty[acc], acc_phase ^ 1u, ctl, prm, true)) break;
-                fence_after();
-                const uint32_t d = tmem + acc * ACC_COLS;
-                for (int kb = 0; kb < num_kb; ++kb) {
-                    if (!wait_bar(&ctl->full_a[stage], phase, ctl, prm, true)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_after();
-                    // K block kb of the pilot starts BK/EPR core matrices (times TS) further on
-                    const uint64_t pd =
-                        pdesc0 + (uint64_t)(8u * F::TS * (uint32_t)(kb * (F::BK / F::EPR)));
-                    const uint64_t yd = ydesc0 + (uint64_t)((stage * (uint32_t)Y_BOX) >> 4);
-#pragma unroll
-                    for (int ks = 0; ks < KSTEPS; ++ks)
-                        umma<DT>(d, pd + (KSTEP_P >> 4) * ks, yd + 2u * ks, idesc,
-                                 (kb | ks) != 0);
-                    umma_commit(&ctl->empty[stage]);
-                    last_bar = &ctl->empty[stage];
-                    last_par = phase;
-                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
-                }
-                if (!ok) break;
-                umma_commit(&ctl->tfull[acc]);
-                last_bar = &ctl->tfull[acc];
-                last_par = acc_phase;
-                acc ^= 1u;
-                if (acc == 0) acc_phase ^= 1u;
-            }
-            if (last_bar) wait_bar(last_bar, last_par, ctl, prm, false);   // drain the MMAs
-        }
-    } else if (warp >= 4) {
-        // --------------------------------------------------------------- epilogue
-        // Warp q owns TMEM lanes 32q .. 32q+31; lane i of the tile holds tile-local lag
-        // TL - 1 - i (reversed order, which makes the pilot tile a Hankel one).
-        const int q = warp & 3;
-        const int o = TL - 1 - (32 * q + lane);          // this thread's lag in the tile
-        uint32_t acc = 0, acc_phase = 0;
-        for (long long t = blockIdx.x; t < prm.num_tiles; t += gridDim.x) {
-            const long long ant0 = (t / num_jt) * (BR / 2);
-            long long j0;
-            int col0, valid;
-            pnce::lag_tile(prm.lags, TL, t % num_jt, j0, col0, valid);
-            int got = 1;
-            if (lane == 0) got = wait_bar_sleepy(&ctl->tfull[acc], acc_phase, ctl, prm);
-            got = __shfl_sync(0xffffffffu, got, 0);
-            if (!got) break;
-            fence_after();
-            const uint32_t tacc = tmem + acc * ACC_COLS + ((uint32_t)(32 * q) << 16);
-            const long long spacing = t + gridDim.x < prm.num_tiles ? prm.epi_spacing : 0;
-            const long long c0 = clock64();
-            float2* hcol = H + col0 + o;
-            for (int c = 0; c < BR / 32; ++c) {              // 32 operand rows = 16 antennas
-                if (c > 0 && spacing > 0) {
-                    // bounded: the target lies at most 8 * spacing cycles after c0
-                    while (clock64() - c0 < c * spacing) __nanosleep(128);
-                }
-                uint32_t v[32];
-                tmem_ld32x32b_x32(tacc + 32u * c, v);
-                tmem_wait_ld();
-                if (c == BR / 32 - 1) {
-                    fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
-                }
-                if (o < valid) {
-#pragma unroll
-                    for (int g = 0; g < 2; ++g) {
-#pragma unroll
-                        for (int a = 0; a < 8; ++a) {
-                            const long long ant = ant0 + 16 * c + 8 * g + a;
-                            if (ant < prm.A) {
-                                const float rs = __ldg(row_scale + ant);
-                                hcol[ant * prm.lags.ldH] =
-                                    make_float2(__uint_as_float(v[16 * g + a]) * rs,
-                                                __uint_as_float(v[16 * g + 8 + a]) * rs);
-                            }
-                        }
-                    }
-                }
-            }
-            acc ^= 1u;
-            if (acc == 0) acc_phase ^= 1u;
-        }
-    }
-
-    fence_before();
-    __syncthreads();
-    if (warp == 2) {
-        fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(TMEM_COLS)
-                     : "memory");
-    }
-}
-
 // ------------------------------------------------ 2-SM variant (CTA pairs, opt-in)
 //
 // tcgen05.mma.cta_group::2 over a cluster of two CTAs: the pair computes a 256-row x BN-lag
@@ -1189,6 +958,281 @@ tc_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restr
     }
 }
 
+// ---------------------------------------- lag-major variant (tiles of <= 128 lags)
+//
+// With the transmitters' cyclic shifts spread out (Eq. 8), a lag tile is one transmitter's
+// L lags; at L = 128 the kernel above would issue MMAs of N = 128, whose operand reads
+// (4 KB of received rows + 4 KB of pilot per 64 clocks) exceed the shared-memory data
+// path.  Here the roles swap: the pilot tile (128 lags x K, the same Hankel core-matrix
+// list, resident for all K blocks) is the A operand and 256 received operand rows
+// (128 antennas, one 32 KB TMA box per K block) are the B operand, so every MMA is again
+// M = 128 x N = 256 (4 KB + 8 KB per 128 clocks).  The accumulator then holds lags in its
+// TMEM lanes and operand rows in its columns: a 32x32b load gives each epilogue thread one
+// lag for 32 operand rows -- the real and imaginary parts of 16 antennas -- and a warp's
+// store writes 32 consecutive lags (256 bytes) of one antenna.
+
+constexpr int BR = 256;                   // operand rows per lag-major tile (the MMA's N)
+constexpr int Y_BOX = BR * 128;           // one TMA box of them: 256 rows x 128 B = 32 KB
+
+// 32 TMEM lanes x 32 columns: thread t receives lane (base + t), columns c .. c+31
+__device__ __forceinline__ void tmem_ld32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+          "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+          "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+          "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+          "=r"(v[31])
+        : "r"(taddr));
+}
+
+// TMA load of a box into the shared memory of every CTA in ctaMask (same offset in each);
+// each destination CTA's barrier at the same offset receives the bytes it got
+__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y,
+                                               unsigned long long* bar, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
+        : "memory");
+}
+// completion of the issuing thread's MMAs arrives on the barrier at this offset in every
+// CTA of ctaMask
+__device__ __forceinline__ void umma_commit_mc(unsigned long long* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster"
+        ".b64 [%0], %1;" ::"r"(su32(bar)), "h"(mask)
+        : "memory");
+}
+
+// CL = 2: a cluster of two CTAs takes two adjacent lag tiles of the same row block; each
+// loads one half of every 256-row stage (128 rows) and multicasts it to both, so the rows
+// are read from L2 once per pair instead of once per CTA (a 256-row stage per 128 MMA
+// clocks per CTA otherwise asks L2 for ~18 TB/s over the GPU).  A stage is free again only
+// when both CTAs' MMAs have read it: the MMA issuers commit to the stage barriers of both.
+template <int DT, int CL>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
+                   const float* __restrict__ row_scale, float2* __restrict__ H,
+                   const TcParams prm) {
+    using F = TcFmt<DT>;
+    constexpr int KSTEPS = 4;                  // MMAs per K block: 128 B of K, 32 B each
+    constexpr int TL = 128;                    // lags per tile (the MMA's M)
+    constexpr uint32_t LBO = 128u * F::TS, SBO = 128u * F::QS;
+    constexpr uint32_t KSTEP_P = 2u * 128u * F::TS;       // pilot bytes per MMA K step
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int nst = prm.stages;
+    unsigned char* sY = base;
+    unsigned char* sP = sY + nst * Y_BOX;
+    Ctl* ctl = reinterpret_cast<Ctl*>(sP + prm.b_region);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int num_jt = prm.num_jt, num_kb = prm.num_kb;
+    // Work units u = unit0 + i * nunits over (row block, lag group); a lag group is CL
+    // adjacent lag tiles, one per CTA of the cluster (rank r takes tile CL * group + r).
+    const uint32_t rank = CL == 2 ? cluster_rank() : 0u;
+    const long long unit0 = CL == 2 ? (long long)cluster_id() : (long long)blockIdx.x;
+    const long long nunits = CL == 2 ? (long long)cluster_count() : (long long)gridDim.x;
+    const int ngroups = num_jt / CL;
+    const long long total_units = prm.num_tiles / CL;
+    const int jt_own = (int)(unit0 % ngroups) * CL + (int)rank;   // fixed: nunits % ngroups == 0
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&ctl->full_a[s], 1);
+            mbar_init(&ctl->empty[s], CL);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl->tfull[b], 1);
+            mbar_init(&ctl->tempty[b], 4);
+        }
+        ctl->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
+                     : "memory");
+    }
+    {
+        // the CTA's lag block is fixed (the grid is a multiple of num_jt): its pilot operand
+        // for every K block, generated once from a shared-memory copy of the bit table
+        long long j0;
+        int col0, valid;
+        pnce::lag_tile(prm.lags, TL, jt_own, j0, col0, valid);
+        if (prm.ext_words <= nst * Y_BOX / 4) {
+            uint32_t* sx = reinterpret_cast<uint32_t*>(sY);
+            for (int i = threadIdx.x; i < prm.ext_words; i += THREADS) sx[i] = __ldg(ext + i);
+            __syncthreads();
+            gen_pilot_rows<DT, true>(sP, sx, prm.N, -j0 - TL + 1, prm.res_rows, threadIdx.x,
+                                     THREADS);
+        } else {
+            gen_pilot_rows<DT>(sP, ext, prm.N, -j0 - TL + 1, prm.res_rows, threadIdx.x, THREADS);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&ctl->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+    if constexpr (CL == 2) cluster_sync_all();   // the peer's barriers are initialised
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ TMA producer
+        if (lane == 0) {
+            uint32_t stage = 0, phase = 0;
+            long long issued = 0;
+            bool ok = true;
+            for (long long u = unit0; u < total_units && ok; u += nunits) {
+                const int y = (int)(u / ngroups) * BR;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!wait_bar(&ctl->empty[stage], phase ^ 1u, ctl, prm, true)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_tx(&ctl->full_a[stage], Y_BOX);
+                    if constexpr (CL == 2) {
+                        // this CTA's half of the rows, into the same place in both CTAs
+                        const int hb = (int)rank * (Y_BOX / 2);
+                        tma_load_2d_mc(sY + stage * Y_BOX + hb, &tmap, kb * F::BK,
+                                       y + (int)rank * (BR / 2), &ctl->full_a[stage], 0x3);
+                    } else {
+                        tma_load_2d(sY + stage * Y_BOX, &tmap, kb * F::BK, y,
+                                    &ctl->full_a[stage]);
+                    }
+                    ++issued;
+                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
+                }
+            }
+            const long long first = issued > nst ? issued - nst : 0;
+            for (long long i = first; i < issued; ++i)
+                wait_bar(&ctl->full_a[i % nst], (uint32_t)((i / nst) & 1), ctl, prm, false);
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | F::AB | ((uint32_t)(BR >> 3) << 17) |
+                                   ((uint32_t)(BM >> 4) << 24);
+            const uint64_t pdesc0 = sdesc(su32(sP), LBO, SBO, 0u);      // A: pilot, Hankel list
+            const uint64_t ydesc0 = sdesc(su32(sY), 16u, 1024u, 2u);    // B: rows, 128B swizzle
+            uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
+            unsigned long long* last_bar = nullptr;
+            uint32_t last_par = 0;
+            bool ok = true;
+            for (long long u = unit0; u < total_units && ok; u += nunits) {
+                if (!wait_bar(&ctl->tempty[acc], acc_phase ^ 1u, ctl, prm, true)) break;
+                fence_after();
+                const uint32_t d = tmem + acc * ACC_COLS;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    if (!wait_bar(&ctl->full_a[stage], phase, ctl, prm, true)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    // K block kb of the pilot starts BK/EPR core matrices (times TS) further on
+                    const uint64_t pd =
+                        pdesc0 + (uint64_t)(8u * F::TS * (uint32_t)(kb * (F::BK / F::EPR)));
+                    const uint64_t yd = ydesc0 + (uint64_t)((stage * (uint32_t)Y_BOX) >> 4);
+#pragma unroll
+                    for (int ks = 0; ks < KSTEPS; ++ks)
+                        umma<DT>(d, pd + (KSTEP_P >> 4) * ks, yd + 2u * ks, idesc,
+                                 (kb | ks) != 0);
+                    if constexpr (CL == 2) umma_commit_mc(&ctl->empty[stage], 0x3);
+                    else umma_commit(&ctl->empty[stage]);
+                    last_bar = &ctl->empty[stage];
+                    last_par = phase;
+                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                umma_commit(&ctl->tfull[acc]);
+                last_bar = &ctl->tfull[acc];
+                last_par = acc_phase;
+                acc ^= 1u;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            if (last_bar) wait_bar(last_bar, last_par, ctl, prm, false);   // drain the MMAs
+        }
+    } else if (warp >= 4) {
+        // --------------------------------------------------------------- epilogue
+        // Warp q owns TMEM lanes 32q .. 32q+31; lane i of the tile holds tile-local lag
+        // TL - 1 - i (reversed order, which makes the pilot tile a Hankel one).
+        const int q = warp & 3;
+        const int o = TL - 1 - (32 * q + lane);          // this thread's lag in the tile
+        uint32_t acc = 0, acc_phase = 0;
+        for (long long u = unit0; u < total_units; u += nunits) {
+            const long long ant0 = (u / ngroups) * (BR / 2);
+            long long j0;
+            int col0, valid;
+            pnce::lag_tile(prm.lags, TL, jt_own, j0, col0, valid);
+            int got = 1;
+            if (lane == 0) got = wait_bar_sleepy(&ctl->tfull[acc], acc_phase, ctl, prm);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) break;
+            fence_after();
+            const uint32_t tacc = tmem + acc * ACC_COLS + ((uint32_t)(32 * q) << 16);
+            const long long spacing = u + nunits < total_units ? prm.epi_spacing : 0;
+            const long long c0 = clock64();
+            float2* hcol = H + col0 + o;
+            for (int c = 0; c < BR / 32; ++c) {              // 32 operand rows = 16 antennas
+                if (c > 0 && spacing > 0) {
+                    // bounded: the target lies at most 8 * spacing cycles after c0
+                    while (clock64() - c0 < c * spacing) __nanosleep(128);
+                }
+                uint32_t v[32];
+                tmem_ld32x32b_x32(tacc + 32u * c, v);
+                tmem_wait_ld();
+                if (c == BR / 32 - 1) {
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&ctl->tempty[acc]);
+                }
+                if (o < valid) {
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+#pragma unroll
+                        for (int a = 0; a < 8; ++a) {
+                            const long long ant = ant0 + 16 * c + 8 * g + a;
+                            if (ant < prm.A) {
+                                const float rs = __ldg(row_scale + ant);
+                                hcol[ant * prm.lags.ldH] =
+                                    make_float2(__uint_as_float(v[16 * g + a]) * rs,
+                                                __uint_as_float(v[16 * g + 8 + a]) * rs);
+                            }
+                        }
+                    }
+                }
+            }
+            acc ^= 1u;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    if (warp == 2) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+    // the peer no longer writes into this CTA's stages or arrives on its barriers
+    if constexpr (CL == 2) cluster_sync_all();
+}
+
 // ------------------------------------------------------------------------- host
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1216,7 +1260,7 @@ unsigned long long wait_limit_ns() {
 template <typename Kern>
 pnce_status launch_kernel(Kern kern, long long grid, size_t smem, cudaStream_t s, bool pdl,
                           const CUtensorMap& map, const uint32_t* ext, const float* factors,
-                          float2* H, const TcParams& prm) {
+                          float2* H, const TcParams& prm, int cluster = 1) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return PNCE_ECUDA;
@@ -1225,11 +1269,22 @@ pnce_status launch_kernel(Kern kern, long long grid, size_t smem, cudaStream_t s
     cfg.blockDim = dim3(THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute at[2];
+    int na = 0;
+    if (cluster > 1) {
+        at[na].id = cudaLaunchAttributeClusterDimension;
+        at[na].val.clusterDim.x = (unsigned)cluster;
+        at[na].val.clusterDim.y = 1;
+        at[na].val.clusterDim.z = 1;
+        ++na;
+    }
+    if (pdl) {
+        at[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        at[na].val.programmaticStreamSerializationAllowed = 1;
+        ++na;
+    }
     cfg.attrs = at;
-    cfg.numAttrs = pdl ? 1 : 0;
+    cfg.numAttrs = na;
     return cudaLaunchKernelEx(&cfg, kern, map, ext, factors, H, prm) == cudaSuccess ? PNCE_OK
                                                                                   : PNCE_ECUDA;
 }
@@ -1257,8 +1312,17 @@ pnce_status launch_lagmajor(const pnce_handle* h, const pnce_pilot* pilot, long 
     prm.err = h->status_dev;
     prm.ext_words = pilot->ext_words;
     prm.drop_first_arrive = 0;
-    long long grid = h->num_sms / njt * njt;             // every CTA keeps one lag block
-    if (grid > prm.num_tiles) grid = prm.num_tiles;      // a multiple of njt as well
+    // CTA pairs sharing each stage by multicast when the lag tiles pair up
+    // (PNCE_TC_LAGMAJOR_CL=1 keeps single CTAs, to compare the two)
+    const char* cl_env = getenv("PNCE_TC_LAGMAJOR_CL");
+    const int cl = (njt % 2 == 0 && njt / 2 <= h->num_sms / 2 && !(cl_env && cl_env[0] == '1'))
+                       ? 2 : 1;
+    // every CTA keeps one lag block: the number of work units (CTAs, or pairs) in flight is
+    // a multiple of the lag groups, and at most the number of units of work
+    const long long groups = njt / cl;
+    long long units = (h->num_sms / cl) / groups * groups;
+    if (units > prm.num_tiles / cl) units = prm.num_tiles / cl;
+    const long long grid = units * cl;
     const long long avail = (long long)h->max_smem_optin - (long long)smem_fixed();
     const long long cm =
         (128 / 8 - 1) * F::QS + ((long long)prm.num_kb * (F::BK / F::EPR) - 1) * F::TS + 1;
@@ -1284,7 +1348,8 @@ pnce_status launch_lagmajor(const pnce_handle* h, const pnce_pilot* pilot, long 
     if (DT == PNCE_TF32) ty = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
     const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)pnce::operand_rows(A)};
     const cuuint64_t strides[1] = {(cuuint64_t)pnce::row_pitch(N) * pnce::elem_bytes(DT)};
-    const cuuint32_t box[2] = {(cuuint32_t)F::BK, (cuuint32_t)BR};
+    // a pair's CTAs load half of the 256 rows each
+    const cuuint32_t box[2] = {(cuuint32_t)F::BK, (cuuint32_t)(BR / cl)};
     const cuuint32_t estr[2] = {1, 1};
     if (enc(&map, ty, 2, const_cast<void*>(operand), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -1292,8 +1357,10 @@ pnce_status launch_lagmajor(const pnce_handle* h, const pnce_pilot* pilot, long 
         return PNCE_ECUDA;
     const size_t smem = smem_fixed() + (size_t)prm.stages * Y_BOX + prm.b_region;
     if ((long long)smem > h->max_smem_optin) return PNCE_EUNSUPPORTED;
-    return launch_kernel(tc_lagmajor_kernel<DT>, grid, smem, s, pdl, map, pilot->ext_bits_dev,
-                         factors, H, prm);
+    return cl == 2 ? launch_kernel(tc_lagmajor_kernel<DT, 2>, grid, smem, s, pdl, map,
+                                   pilot->ext_bits_dev, factors, H, prm, 2)
+                   : launch_kernel(tc_lagmajor_kernel<DT, 1>, grid, smem, s, pdl, map,
+                                   pilot->ext_bits_dev, factors, H, prm);
 }
 
 template <int DT>

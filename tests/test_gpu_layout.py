@@ -77,3 +77,28 @@ def test_layout_rejects_aliasing():
     with pytest.raises(pk.PnceError) as e:
         pk.estimate(Y, pilot, 4, 40, cp_len=8, shift_rule="spread")    # 40 > 127 // 4
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("dtype", ["fp16", "bf16", "e4m3", "tf32"])
+def test_spread_kernels_agree(dtype, monkeypatch):
+    # the even-spread tiles of 128 lags or fewer go to the lag-major kernel (CTA pairs that
+    # share each stage by multicast, or single CTAs); all three forms give the same bits as
+    # the lag-column kernel, across several row blocks, a ragged antenna count and odd
+    # numbers of lag tiles per pair
+    import paper_2206_05506_gb300 as pk
+    dev = torch.device("cuda", 0)
+    for (r, M, K, L, cp, F) in [(11, 37, 4, 128, 0, 5), (11, 16, 6, 100, 0, 9),
+                                (12, 130, 16, 128, 0, 3), (10, 64, 3, 64, 64, 4)]:
+        bits, h, Y, sh = _case(r, M, K, L, cp, F, "spread")
+        pilot = pk.Pilot(bits, device=dev)
+        Yd = torch.from_numpy(Y).to(dev)
+        outs = []
+        for lm, cl in (("0", "2"), ("1", "1"), ("1", "2")):
+            monkeypatch.setenv("PNCE_TC_LAGMAJOR", lm)
+            monkeypatch.setenv("PNCE_TC_LAGMAJOR_CL", cl)
+            outs.append(pk.estimate(Yd, pilot, K, L, dtype=dtype, cp_len=cp,
+                                    shift_rule="spread"))
+        assert pk.get_status(dev) == 0
+        assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2]), (r, M, K, L)
+        ref = O.estimate_general(Y, bits, K, L, cp_len=cp, shifts=sh)
+        assert O.nmse(outs[2].cpu().numpy(), ref) <= TOL[dtype]
