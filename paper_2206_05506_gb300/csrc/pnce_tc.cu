@@ -1233,6 +1233,236 @@ tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __r
     if constexpr (CL == 2) cluster_sync_all();
 }
 
+// Lag-major tiles on CTA pairs with the 2-SM MMA (tcgen05.mma.cta_group::2, M = 256):
+// each CTA of a cluster holds its own lag tile's pilot list (the A rows of its half of M)
+// and TMA-loads its own half of the 256 received rows (the B columns of its half of N), so
+// an SM writes 32 B/clock of rows into shared memory and its tensor core reads 64 B/clock
+// of operands -- in the single-CTA lag-major kernel the 256-row stages alone asked for
+// 64 B/clock of writes on top of 96 B/clock of reads, beyond the 128 B/clock data path.
+// Rank 0 issues the MMAs of the pair; both CTAs' loads complete on rank 0's stage
+// barrier; MMA completion arrives on the barriers of both; each CTA drains its own lags
+// for all 256 rows, rank 1 releasing rank 0's accumulator barrier remotely.
+template <int DT, int KPS>
+__global__ void __launch_bounds__(THREADS, 1)
+tc_lagmajor_pair_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
+                        const float* __restrict__ row_scale, float2* __restrict__ H,
+                        const TcParams prm) {
+    using F = TcFmt<DT>;
+    constexpr int KSTEPS = 4;
+    constexpr int TL = 128;
+    constexpr uint32_t LBO = 128u * F::TS, SBO = 128u * F::QS;
+    constexpr uint32_t KSTEP_P = 2u * 128u * F::TS;
+    constexpr int a_stage = KPS * A_BOX;        // this CTA's 128 rows of KPS K blocks
+
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const int nst = prm.stages;
+    unsigned char* sY = base;
+    unsigned char* sP = sY + nst * a_stage;
+    PairCtl* ctl = reinterpret_cast<PairCtl*>(sP + prm.b_region);
+    Ctl* wctl = reinterpret_cast<Ctl*>(ctl);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int num_jt = prm.num_jt, num_st = prm.num_st;
+    const uint32_t rank = cluster_rank();
+    const long long unit0 = cluster_id(), nunits = cluster_count();
+    const int ngroups = num_jt / 2;
+    const long long total_units = prm.num_tiles / 2;
+    const int jt_own = (int)(unit0 % ngroups) * 2 + (int)rank;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < nst; ++s) {
+            mbar_init(&ctl->full_a[s], 1);
+            mbar_init(&ctl->empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&ctl->tfull[b], 1);
+            mbar_init(&ctl->tempty[b], 8);
+        }
+        ctl->abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 0 && lane == 0) {
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap))
+                     : "memory");
+    }
+    {
+        long long j0;
+        int col0, valid;
+        pnce::lag_tile(prm.lags, TL, jt_own, j0, col0, valid);
+        if (prm.ext_words <= nst * a_stage / 4) {
+            uint32_t* sx = reinterpret_cast<uint32_t*>(sY);
+            for (int i = threadIdx.x; i < prm.ext_words; i += THREADS) sx[i] = __ldg(ext + i);
+            __syncthreads();
+            gen_pilot_rows<DT, true>(sP, sx, prm.N, -j0 - TL + 1, prm.res_rows, threadIdx.x,
+                                     THREADS);
+        } else {
+            gen_pilot_rows<DT>(sP, ext, prm.N, -j0 - TL + 1, prm.res_rows, threadIdx.x, THREADS);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         su32(&ctl->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync_all();      // barriers of both CTAs initialised, both pilot lists built
+    fence_after();
+    const uint32_t tmem = ctl->tmem_base;
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+
+    if (warp == 0) {
+        // ------------------------------------------------- TMA producer (both CTAs)
+        if (lane == 0) {
+            const uint32_t full0 = cluster_addr(&ctl->full_a[0], 0);
+            uint32_t stage = 0, phase = 0;
+            long long issued = 0;
+            bool ok = true;
+            for (long long u = unit0; u < total_units && ok; u += nunits) {
+                const int y = (int)(u / ngroups) * BR + (int)rank * BM;
+                for (int st = 0; st < num_st; ++st) {
+                    if (!wait_bar(&ctl->empty[stage], phase ^ 1u, wctl, prm, true)) {
+                        ok = false;
+                        break;
+                    }
+                    if (rank == 0) mbar_arrive_tx(&ctl->full_a[stage], 2 * a_stage);
+#pragma unroll
+                    for (int h = 0; h < KPS; ++h)
+                        tma_load_2d_pair(sY + stage * a_stage + h * A_BOX, &tmap,
+                                         (KPS * st + h) * F::BK, y,
+                                         full0 + stage * (uint32_t)sizeof(unsigned long long));
+                    ++issued;
+                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
+                }
+            }
+            if (rank == 0) {
+                const long long first = issued > nst ? issued - nst : 0;
+                for (long long i = first; i < issued; ++i)
+                    wait_bar<true>(&ctl->full_a[i % nst], (uint32_t)((i / nst) & 1), wctl, prm,
+                                   false);
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------ MMA issuer (rank 0 only)
+        if (rank == 0 && lane == 0) {
+            const uint32_t idesc = (1u << 4) | F::AB | ((uint32_t)(BR >> 3) << 17) |
+                                   ((uint32_t)(2 * BM >> 4) << 24);
+            const uint64_t pdesc0 = sdesc(su32(sP), LBO, SBO, 0u);     // A: pilot lists
+            const uint64_t ydesc0 = sdesc(su32(sY), 16u, 1024u, 2u);   // B: row halves
+            uint32_t stage = 0, phase = 0, acc = 0, acc_phase = 0;
+            unsigned long long* last_bar = nullptr;
+            uint32_t last_par = 0;
+            bool ok = true;
+            for (long long u = unit0; u < total_units && ok; u += nunits) {
+                if (!wait_bar<true>(&ctl->tempty[acc], acc_phase ^ 1u, wctl, prm, true)) break;
+                fence_after();
+                const uint32_t d = tmem + acc * ACC_COLS;
+                for (int st = 0; st < num_st; ++st) {
+                    if (!wait_bar<true>(&ctl->full_a[stage], phase, wctl, prm, true)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint64_t yd = ydesc0 + (uint64_t)((stage * (uint32_t)a_stage) >> 4);
+                    const uint64_t pd =
+                        pdesc0 + (uint64_t)(8u * F::TS * (uint32_t)(KPS * st * (F::BK / F::EPR)));
+#pragma unroll
+                    for (int h = 0; h < KPS; ++h)
+#pragma unroll
+                        for (int ks = 0; ks < KSTEPS; ++ks)
+                            umma_pair<DT>(d,
+                                          pd + (uint64_t)(h * 8 * F::TS * (F::BK / F::EPR)) +
+                                              (KSTEP_P >> 4) * ks,
+                                          yd + (uint64_t)(h * (A_BOX >> 4)) + 2u * ks, idesc,
+                                          (st | h | ks) != 0);
+                    umma_commit_pair(&ctl->empty[stage]);
+                    last_bar = &ctl->empty[stage];
+                    last_par = phase;
+                    if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
+                }
+                if (!ok) break;
+                umma_commit_pair(&ctl->tfull[acc]);
+                last_bar = &ctl->tfull[acc];
+                last_par = acc_phase;
+                acc ^= 1u;
+                if (acc == 0) acc_phase ^= 1u;
+            }
+            if (last_bar) wait_bar(last_bar, last_par, wctl, prm, false);
+        }
+    } else if (warp >= 4) {
+        // ------------------------------------------------------ epilogue (both CTAs)
+        // lanes: this CTA's 128 lags (lane i holds tile-local lag TL - 1 - i); columns:
+        // the pair's 256 operand rows (128 antennas)
+        const int q = warp & 3;
+        const int o = TL - 1 - (32 * q + lane);
+        uint32_t acc = 0, acc_phase = 0;
+        long long j0;
+        int col0, valid;
+        pnce::lag_tile(prm.lags, TL, jt_own, j0, col0, valid);
+        for (long long u = unit0; u < total_units; u += nunits) {
+            const long long ant0 = (u / ngroups) * (BR / 2);
+            int got = 1;
+            if (lane == 0) got = wait_bar_sleepy(&ctl->tfull[acc], acc_phase, wctl, prm);
+            got = __shfl_sync(0xffffffffu, got, 0);
+            if (!got) break;
+            fence_after();
+            const uint32_t tacc = tmem + acc * ACC_COLS + ((uint32_t)(32 * q) << 16);
+            const long long spacing = u + nunits < total_units ? prm.epi_spacing : 0;
+            const long long c0 = clock64();
+            float2* hcol = H + col0 + o;
+            for (int c = 0; c < BR / 32; ++c) {
+                if (c > 0 && spacing > 0) {
+                    // bounded: the target lies at most 8 * spacing cycles after c0
+                    while (clock64() - c0 < c * spacing) __nanosleep(128);
+                }
+                uint32_t v[32];
+                tmem_ld32x32b_x32(tacc + 32u * c, v);
+                tmem_wait_ld();
+                if (c == BR / 32 - 1) {
+                    fence_before();
+                    __syncwarp();
+                    if (lane == 0) {
+                        if (rank == 0) mbar_arrive(&ctl->tempty[acc]);
+                        else mbar_arrive_remote(&ctl->tempty[acc], 0);
+                    }
+                }
+                if (o < valid) {
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+#pragma unroll
+                        for (int a = 0; a < 8; ++a) {
+                            const long long ant = ant0 + 16 * c + 8 * g + a;
+                            if (ant < prm.A) {
+                                const float rs = __ldg(row_scale + ant);
+                                hcol[ant * prm.lags.ldH] =
+                                    make_float2(__uint_as_float(v[16 * g + a]) * rs,
+                                                __uint_as_float(v[16 * g + 8 + a]) * rs);
+                            }
+                        }
+                    }
+                }
+            }
+            acc ^= 1u;
+            if (acc == 0) acc_phase ^= 1u;
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    cluster_sync_all();      // the peer no longer reads this CTA's shared memory or barriers
+    if (warp == 2) {
+        fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TMEM_COLS)
+                     : "memory");
+    }
+}
+
 // ------------------------------------------------------------------------- host
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -1312,11 +1542,13 @@ pnce_status launch_lagmajor(const pnce_handle* h, const pnce_pilot* pilot, long 
     prm.err = h->status_dev;
     prm.ext_words = pilot->ext_words;
     prm.drop_first_arrive = 0;
-    // CTA pairs sharing each stage by multicast when the lag tiles pair up
-    // (PNCE_TC_LAGMAJOR_CL=1 keeps single CTAs, to compare the two)
+    // CTA pairs when the lag tiles pair up: by default with the 2-SM MMA, each CTA loading
+    // half of the rows; PNCE_TC_LAGMAJOR_CL=2 pairs that share 256-row stages by multicast,
+    // =1 single CTAs (to compare the three)
     const char* cl_env = getenv("PNCE_TC_LAGMAJOR_CL");
-    const int cl = (njt % 2 == 0 && njt / 2 <= h->num_sms / 2 && !(cl_env && cl_env[0] == '1'))
-                       ? 2 : 1;
+    const bool pairable = njt % 2 == 0 && njt / 2 <= h->num_sms / 2;
+    const int cl = pairable && !(cl_env && cl_env[0] == '1') ? 2 : 1;
+    const bool mma2 = cl == 2 && !(cl_env && cl_env[0] == '2');
     // every CTA keeps one lag block: the number of work units (CTAs, or pairs) in flight is
     // a multiple of the lag groups, and at most the number of units of work
     const long long groups = njt / cl;
@@ -1324,16 +1556,31 @@ pnce_status launch_lagmajor(const pnce_handle* h, const pnce_pilot* pilot, long 
     if (units > prm.num_tiles / cl) units = prm.num_tiles / cl;
     const long long grid = units * cl;
     const long long avail = (long long)h->max_smem_optin - (long long)smem_fixed();
-    const long long cm =
-        (128 / 8 - 1) * F::QS + ((long long)prm.num_kb * (F::BK / F::EPR) - 1) * F::TS + 1;
-    const long long bregion = (cm * 128 + 1023) / 1024 * 1024;
-    long long st = (avail - bregion) / Y_BOX;
-    if (st < 3) return PNCE_EUNSUPPORTED;
+    // The resident pilot list must cover every K block the MMAs read: with kps K blocks per
+    // stage that is the K blocks rounded up to a multiple of kps (a last stage past N reads
+    // zero rows, but its pilot core matrices must still lie inside the list).
+    auto list_cm = [&](int kps_) {
+        const long long kb = ((long long)prm.num_kb + kps_ - 1) / kps_ * kps_;
+        return (128 / 8 - 1) * F::QS + (kb * (F::BK / F::EPR) - 1) * F::TS + 1;
+    };
+    auto region = [](long long cm_) { return (cm_ * 128 + 1023) / 1024 * 1024; };
+    // stage bytes per CTA: the whole 256-row box, or (2-SM pairs) this CTA's 128 rows of
+    // two K blocks when three such stages fit, else of one K block
+    int kps = 1;
+    long long stage_bytes = Y_BOX;
+    if (mma2) {
+        kps = (avail - region(list_cm(2))) / (2 * A_BOX) >= 3 ? 2 : 1;
+        stage_bytes = kps * A_BOX;
+    }
+    const long long cm = list_cm(kps);
+    const long long bregion = region(cm);
+    long long st = (avail - bregion) / stage_bytes;
+    if (st < (kps == 2 ? 3 : (mma2 ? 4 : 3))) return PNCE_EUNSUPPORTED;
     if (st > STAGES) st = STAGES;
     if ((prm.num_tiles + grid - 1) / grid <= 1 && st > 4) st = 4;
-    prm.kps = 1;
-    prm.a_stage = Y_BOX;
-    prm.num_st = prm.num_kb;
+    prm.kps = kps;
+    prm.a_stage = (int)stage_bytes;
+    prm.num_st = (prm.num_kb + kps - 1) / kps;
     prm.stages = (int)st;
     prm.b_region = (int)bregion;
     prm.res_rows = (int)(cm * 8);
@@ -1355,8 +1602,13 @@ pnce_status launch_lagmajor(const pnce_handle* h, const pnce_pilot* pilot, long 
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return PNCE_ECUDA;
-    const size_t smem = smem_fixed() + (size_t)prm.stages * Y_BOX + prm.b_region;
+    const size_t smem = smem_fixed() + (size_t)prm.stages * prm.a_stage + prm.b_region;
     if ((long long)smem > h->max_smem_optin) return PNCE_EUNSUPPORTED;
+    if (mma2)
+        return kps == 2 ? launch_kernel(tc_lagmajor_pair_kernel<DT, 2>, grid, smem, s, pdl, map,
+                                        pilot->ext_bits_dev, factors, H, prm, 2)
+                        : launch_kernel(tc_lagmajor_pair_kernel<DT, 1>, grid, smem, s, pdl, map,
+                                        pilot->ext_bits_dev, factors, H, prm, 2);
     return cl == 2 ? launch_kernel(tc_lagmajor_kernel<DT, 2>, grid, smem, s, pdl, map,
                                    pilot->ext_bits_dev, factors, H, prm, 2)
                    : launch_kernel(tc_lagmajor_kernel<DT, 1>, grid, smem, s, pdl, map,
