@@ -320,12 +320,34 @@ simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict
 
 // Few lags (K*L <= 32, lags contiguous): the block tile above would leave most lanes idle,
 // and at ~2 K*L flops per 8-byte sample the work is close to the HBM roofline.  One warp
-// per received row: lane l takes samples l, l+32, ... (coalesced 8-byte loads, read once)
-// and reads the pilot bits b[n-K*L+1 .. n] as one window of the wrapped bit table.  With
+// per received row: lane l takes the sample pairs (2p, 2p+1) for p = l, l+32, ... (four
+// pairs in flight per lane, each sample read once; one 16-byte load per pair when the
+// row is 16-byte aligned, two 8-byte loads otherwise -- the pairs, and so the order of
+// every sum, do not depend on where the row lies, so the same row gives the same bits in
+// any buffer) and reads the pilot bits of each sample as one window of the wrapped bit
+// table.  With
 // p = 1 - 2b, sum_n y[n] p[n-j] = S - 2 B_j, S = sum_n y[n] and B_j the sum of the samples
 // whose bit b[n-j] is set, so each lag costs one bit test and one predicated packed add.
 // A butterfly reduction over the warp (the same sum on every lane) ends the row and lane
 // j stores lag j.
+template <int KLM>
+__device__ __forceinline__ void few_lags_sample(const uint32_t* __restrict__ ext, int N, int KL,
+                                                int n, float2 v, float2& all,
+                                                float2 (&acc)[KLM]) {
+    // bits of samples n-KL+1 .. n (mod N): bit i of w is pilot bit q + i, and lag j meets
+    // bit n - j, i.e. bit KL-1-j of w; the table wraps past N, so q < N keeps the window
+    // inside it
+    int q = n - (KL - 1);
+    if (q < 0) q += N;
+    const uint32_t lo = __ldg(ext + (q >> 5)), hi = __ldg(ext + (q >> 5) + 1);
+    const uint32_t w = (uint32_t)((((uint64_t)hi << 32) | lo) >> (q & 31));
+    all = __fadd2_rn(all, v);
+    const uint32_t wr = __brev(w) >> (32 - KL);     // bit j of wr = bit KL-1-j of w
+#pragma unroll
+    for (int j = 0; j < KLM; ++j)
+        if ((wr >> j) & 1u) acc[j] = __fadd2_rn(acc[j], v);
+}
+
 template <int KLM>
 __global__ void __launch_bounds__(256)
 simt_few_lags_kernel(const uint32_t* __restrict__ ext, const float2* __restrict__ Y,
@@ -340,24 +362,37 @@ simt_few_lags_kernel(const uint32_t* __restrict__ ext, const float2* __restrict_
         float2 all = make_float2(0.f, 0.f);     // S
 #pragma unroll
         for (int j = 0; j < KLM; ++j) acc[j] = make_float2(0.f, 0.f);
-        // several samples in flight per lane (the loads are the latency to hide)
-#pragma unroll (KLM >= 16 ? 4 : 2)
-        for (int n = lane; n < N; n += 32) {
-            const float2 v = __ldcs(y + n);
-            // bits of samples n-KL+1 .. n (mod N): bit i of w is pilot bit q + i, and lag
-            // j meets bit n - j, i.e. bit KL-1-j of w; the table wraps past N, so q < N
-            // keeps the window inside it
-            int q = n - (KL - 1);
-            if (q < 0) q += N;
-            const uint32_t lo = __ldg(ext + (q >> 5)), hi = __ldg(ext + (q >> 5) + 1);
-            const uint32_t w = (uint32_t)((((uint64_t)hi << 32) | lo) >> (q & 31));
-            all = __fadd2_rn(all, v);
-            // lag j: bit KL-1-j of w; reversed so that the bit test is by a constant
-            const uint32_t wr = __brev(w) >> (32 - KL);     // bit j of wr = bit KL-1-j of w
+        const bool al16 = ((uintptr_t)y & 15u) == 0;
+        const int npairs = N >> 1;
+        for (int p0 = lane; p0 < npairs; p0 += 4 * 32) {
+            float4 v[4];
 #pragma unroll
-            for (int j = 0; j < KLM; ++j)
-                if ((wr >> j) & 1u) acc[j] = __fadd2_rn(acc[j], v);
+            for (int u = 0; u < 4; ++u) {               // the loads first: latency to hide
+                const int p = p0 + 32 * u;
+                v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (p < npairs) {
+                    if (al16) {
+                        v[u] = __ldcs(reinterpret_cast<const float4*>(y) + p);
+                    } else {
+                        const float2 a0 = __ldcs(y + 2 * p), a1 = __ldcs(y + 2 * p + 1);
+                        v[u] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = p0 + 32 * u;
+                if (p < npairs) {
+                    few_lags_sample<KLM>(ext, N, KL, 2 * p, make_float2(v[u].x, v[u].y), all,
+                                         acc);
+                    few_lags_sample<KLM>(ext, N, KL, 2 * p + 1, make_float2(v[u].z, v[u].w),
+                                         all, acc);
+                }
+            }
         }
+        // an odd last sample: the lane whose turn pair npairs would be
+        if ((N & 1) && lane == (npairs & 31))
+            few_lags_sample<KLM>(ext, N, KL, N - 1, __ldcs(y + N - 1), all, acc);
         float2 mine = make_float2(0.f, 0.f);
 #pragma unroll
         for (int j = 0; j < KLM; ++j) {

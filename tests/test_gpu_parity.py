@@ -331,3 +331,22 @@ def test_auto_dtype_follows_its_rule(pk):
         Hh = pk.estimate_host(torch.from_numpy(Y).pin_memory(), pilot, K, L, dtype="auto")
         assert torch.equal(Hh, Hw.cpu()), shape
     assert pk.get_status(dev) == 0
+
+
+@pytest.mark.parametrize("KL", [1, 7, 16, 32])
+def test_few_lags_result_independent_of_row_placement(pk, KL):
+    # the few-lags FP32 kernel reads rows of odd N that alternately start on and half-way
+    # into a 16-byte boundary; a row shifted by one position in the batch (so its start
+    # flips between the two) must give the same bits, for even and odd N
+    dev = torch.device("cuda", 0)
+    for r in (6, 9):
+        bits, _, Y = _case(r, 5, 1, KL, 2, seed=4)
+        F, M, N = Y.shape
+        pilot = pk.Pilot(bits, device=dev)
+        Yd = torch.from_numpy(Y).to(dev)
+        H = pk.estimate(Yd, pilot, 1, KL, dtype="fp32")
+        Y2 = torch.cat([torch.zeros((1, 1, N), dtype=torch.complex64, device=dev),
+                        Yd.reshape(1, F * M, N)], dim=1)
+        H2 = pk.estimate(Y2, pilot, 1, KL, dtype="fp32").reshape(F * M + 1, 1, KL)
+        assert torch.equal(H2[1:], H.reshape(F * M, 1, KL))
+        assert O.nmse(H.cpu().numpy(), O.estimate(Y, bits, 1, KL)) <= 1e-10
