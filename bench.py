@@ -654,6 +654,8 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=8, help="frames per reference step")
     ap.add_argument("--serving-seconds", type=float, default=10.0,
                     help="length of the Poisson serving trace (0: skip)")
+    ap.add_argument("--serving-sweep", type=int, default=1,
+                    help="also sweep the offered rate of the serving trace (1/0)")
     ap.add_argument("--differentiation", type=int, default=1,
                     help="also time the relaxed-pilot forward + adjoint (1/0)")
     ap.add_argument("--yardsticks", type=int, default=1,
@@ -847,7 +849,8 @@ def main():
         refs = {}
         Href = None
 
-    serving = (run_serving(dev, args.serving_seconds, refs=refs.get("serving"))
+    serving = (run_serving(dev, args.serving_seconds, refs=refs.get("serving"),
+                           sweep_rates=SWEEP_RATES_HZ if args.serving_sweep else ())
                if args.serving_seconds > 0 and single else None)
     small = run_small_case(dev, ref=refs.get("small")) if args.small_case and single else None
     differentiation = run_differentiation(dev) if args.differentiation and single else None

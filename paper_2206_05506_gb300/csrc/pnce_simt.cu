@@ -393,20 +393,35 @@ simt_few_lags_kernel(const uint32_t* __restrict__ ext, const float2* __restrict_
         // an odd last sample: the lane whose turn pair npairs would be
         if ((N & 1) && lane == (npairs & 31))
             few_lags_sample<KLM>(ext, N, KL, N - 1, __ldcs(y + N - 1), all, acc);
-        float2 mine = make_float2(0.f, 0.f);
+        // S over the warp, and B_j over the warp by a reduce-scatter: at each exchange
+        // distance o the lanes split the remaining lags in halves, keep one half and send
+        // the other, so lane j ends with the warp's B_j after 31 exchanges per part (a
+        // butterfly per lag would chain 5 * K*L of them)
 #pragma unroll
-        for (int j = 0; j < KLM; ++j) {
-            if (j < KL) {                                  // uniform over the warp
-                float re = all.x - 2.f * acc[j].x, im = all.y - 2.f * acc[j].y;
+        for (int o = 16; o; o >>= 1) {
+            all.x += __shfl_xor_sync(0xffffffffu, all.x, o);
+            all.y += __shfl_xor_sync(0xffffffffu, all.y, o);
+        }
+        float bx[32], by[32];
 #pragma unroll
-                for (int o = 16; o; o >>= 1) {
-                    re += __shfl_xor_sync(0xffffffffu, re, o);
-                    im += __shfl_xor_sync(0xffffffffu, im, o);
-                }
-                if (lane == j) mine = make_float2(re * invN, im * invN);
+        for (int j = 0; j < 32; ++j) {
+            bx[j] = j < KLM ? acc[j].x : 0.f;
+            by[j] = j < KLM ? acc[j].y : 0.f;
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < o; ++i) {
+                const float sx = upper ? bx[i] : bx[i + o], kx = upper ? bx[i + o] : bx[i];
+                const float sy = upper ? by[i] : by[i + o], ky = upper ? by[i + o] : by[i];
+                bx[i] = kx + __shfl_xor_sync(0xffffffffu, sx, o);
+                by[i] = ky + __shfl_xor_sync(0xffffffffu, sy, o);
             }
         }
-        if (lane < KL) H[a * ldH + lane] = mine;
+        if (lane < KL)
+            H[a * ldH + lane] =
+                make_float2((all.x - 2.f * bx[0]) * invN, (all.y - 2.f * by[0]) * invN);
     }
 }
 
