@@ -330,6 +330,53 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
     return res
 
 
+# One-request serving batches: (M, N, K, L) of a large and a small request
+SERVING_BATCH_CASES = ((256, 1023, 1, 1023), (64, 511, 4, 32))
+
+
+def run_serving_batch(dev, replays: int):
+    """GPU time of one serving batch holding a single request, per path (fp16 tensor
+    cores, FP32 SIMT) and request shape: a one-stream engine replays the batch's captured
+    graph (prep, gather + quantise or gather, correlation, scatter), each replay reading a
+    different page-locked block from a pool larger than L2 and writing its result to
+    page-locked memory; CUDA events around each replay, median and 90th percentile."""
+    import torch
+
+    from paper_2206_05506_gb300 import serve
+    from synth import serving as S
+
+    out = {}
+    gen = torch.Generator().manual_seed(0)
+    for M, N, K, L in SERVING_BATCH_CASES:
+        blocks = max(2, (320 << 20) // (M * N * 8))          # 320 MB of received blocks
+        pool = torch.randn((blocks, M, N), dtype=torch.complex64, generator=gen).pin_memory()
+        H = torch.empty((M, K * L), dtype=torch.complex64).pin_memory()
+        for dtype in ("fp16", "fp32"):
+            eng = serve.GpuEngine(S.pilot_bits, device=dev, dtype=dtype, slots=1)
+            cap = next(c for c in serve.CAPACITIES if c >= M)
+            shape = eng._shape(0, N, serve.kl_class(K * L, N), cap)
+            s = eng.streams[0]
+            ts = []
+            for i in range(replays + 20):
+                req = [serve.Request(0, 0.0, M, N, K, L, pool[i % blocks].data_ptr(),
+                                     H.data_ptr())]
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                shape.run(eng, 0, req)
+                e1.record(s)
+                e1.synchronize()
+                if i >= 20:
+                    ts.append(e0.elapsed_time(e1) * 1e3)
+            out[f"{dtype}_m{M}_n{N}_kl{K * L}"] = {
+                "gpu_us_median": float(np.median(ts)),
+                "gpu_us_p90": float(np.percentile(ts, 90)), "replays": replays,
+                "bytes_in": M * N * 8, "bytes_out": M * K * L * 8}
+            del eng
+        del pool
+    return out
+
+
 def run_paper_scale(dev, ref=None, reps: int = 50):
     """The paper-scale workload (M = 64, N = 1023, K = 8, L = 64, 128 frames, SNR 0/10/20
     dB): the plain FP32 SIMT path against the TF32 tensor-core path (and fp16), each with
@@ -656,6 +703,8 @@ def main():
                     help="length of the Poisson serving trace (0: skip)")
     ap.add_argument("--serving-sweep", type=int, default=1,
                     help="also sweep the offered rate of the serving trace (1/0)")
+    ap.add_argument("--serving-batch-replays", type=int, default=300,
+                    help="replays per case of a one-request serving batch (0: skip)")
     ap.add_argument("--differentiation", type=int, default=1,
                     help="also time the relaxed-pilot forward + adjoint (1/0)")
     ap.add_argument("--yardsticks", type=int, default=1,
@@ -852,6 +901,8 @@ def main():
     serving = (run_serving(dev, args.serving_seconds, refs=refs.get("serving"),
                            sweep_rates=SWEEP_RATES_HZ if args.serving_sweep else ())
                if args.serving_seconds > 0 and single else None)
+    serving_batch = (run_serving_batch(dev, args.serving_batch_replays)
+                     if args.serving_batch_replays > 0 and single else None)
     small = run_small_case(dev, ref=refs.get("small")) if args.small_case and single else None
     differentiation = run_differentiation(dev) if args.differentiation and single else None
 
@@ -919,6 +970,7 @@ def main():
         "accuracy": accuracy,
         "cpu_baseline": cpu,
         "serving": serving,
+        "serving_batch": serving_batch,
         "small_case": small,
         "other_dtypes": others,
         "paper_scale": paper_scale,
