@@ -990,31 +990,11 @@ __device__ __forceinline__ void tmem_ld32x32b_x32(uint32_t taddr, uint32_t (&v)[
         : "r"(taddr));
 }
 
-// TMA load of a box into the shared memory of every CTA in ctaMask (same offset in each);
-// each destination CTA's barrier at the same offset receives the bytes it got
-__device__ __forceinline__ void tma_load_2d_mc(void* dst, const CUtensorMap* map, int x, int y,
-                                               unsigned long long* bar, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(su32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(su32(bar)), "h"(mask)
-        : "memory");
-}
-// completion of the issuing thread's MMAs arrives on the barrier at this offset in every
-// CTA of ctaMask
-__device__ __forceinline__ void umma_commit_mc(unsigned long long* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster"
-        ".b64 [%0], %1;" ::"r"(su32(bar)), "h"(mask)
-        : "memory");
-}
-
-// CL = 2: a cluster of two CTAs takes two adjacent lag tiles of the same row block; each
-// loads one half of every 256-row stage (128 rows) and multicasts it to both, so the rows
-// are read from L2 once per pair instead of once per CTA (a 256-row stage per 128 MMA
-// clocks per CTA otherwise asks L2 for ~18 TB/s over the GPU).  A stage is free again only
-// when both CTAs' MMAs have read it: the MMA issuers commit to the stage barriers of both.
-template <int DT, int CL>
+// Lag-major tiles on single CTAs: the pilot is the A operand (128 lags, M), the received
+// rows the B operand (256 rows, N), so a warp of the epilogue stores 32 consecutive lags of
+// one antenna.  A CTA streams a 256-row stage per 128 MMA clocks, twice the contiguous
+// kernel's rate; the 2-SM pair kernel below halves that per SM and is the default.
+template <int DT>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __restrict__ ext,
                    const float* __restrict__ row_scale, float2* __restrict__ H,
@@ -1034,19 +1014,17 @@ tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __r
     Ctl* ctl = reinterpret_cast<Ctl*>(sP + prm.b_region);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int num_jt = prm.num_jt, num_kb = prm.num_kb;
-    // Work units u = unit0 + i * nunits over (row block, lag group); a lag group is CL
-    // adjacent lag tiles, one per CTA of the cluster (rank r takes tile CL * group + r).
-    const uint32_t rank = CL == 2 ? cluster_rank() : 0u;
-    const long long unit0 = CL == 2 ? (long long)cluster_id() : (long long)blockIdx.x;
-    const long long nunits = CL == 2 ? (long long)cluster_count() : (long long)gridDim.x;
-    const int ngroups = num_jt / CL;
-    const long long total_units = prm.num_tiles / CL;
-    const int jt_own = (int)(unit0 % ngroups) * CL + (int)rank;   // fixed: nunits % ngroups == 0
+    // Work units u = unit0 + i * nunits over (row block, lag tile); the CTA's lag tile is
+    // fixed because the grid is a multiple of the lag tiles.
+    const long long unit0 = blockIdx.x, nunits = gridDim.x;
+    const int ngroups = num_jt;
+    const long long total_units = prm.num_tiles;
+    const int jt_own = (int)(unit0 % ngroups);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < nst; ++s) {
             mbar_init(&ctl->full_a[s], 1);
-            mbar_init(&ctl->empty[s], CL);
+            mbar_init(&ctl->empty[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&ctl->tfull[b], 1);
@@ -1088,7 +1066,6 @@ tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __r
     __syncthreads();
     fence_after();
     const uint32_t tmem = ctl->tmem_base;
-    if constexpr (CL == 2) cluster_sync_all();   // the peer's barriers are initialised
     asm volatile("griddepcontrol.wait;" ::: "memory");
 
     if (warp == 0) {
@@ -1105,15 +1082,7 @@ tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __r
                         break;
                     }
                     mbar_arrive_tx(&ctl->full_a[stage], Y_BOX);
-                    if constexpr (CL == 2) {
-                        // this CTA's half of the rows, into the same place in both CTAs
-                        const int hb = (int)rank * (Y_BOX / 2);
-                        tma_load_2d_mc(sY + stage * Y_BOX + hb, &tmap, kb * F::BK,
-                                       y + (int)rank * (BR / 2), &ctl->full_a[stage], 0x3);
-                    } else {
-                        tma_load_2d(sY + stage * Y_BOX, &tmap, kb * F::BK, y,
-                                    &ctl->full_a[stage]);
-                    }
+                    tma_load_2d(sY + stage * Y_BOX, &tmap, kb * F::BK, y, &ctl->full_a[stage]);
                     ++issued;
                     if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
                 }
@@ -1151,8 +1120,7 @@ tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __r
                     for (int ks = 0; ks < KSTEPS; ++ks)
                         umma<DT>(d, pd + (KSTEP_P >> 4) * ks, yd + 2u * ks, idesc,
                                  (kb | ks) != 0);
-                    if constexpr (CL == 2) umma_commit_mc(&ctl->empty[stage], 0x3);
-                    else umma_commit(&ctl->empty[stage]);
+                    umma_commit(&ctl->empty[stage]);
                     last_bar = &ctl->empty[stage];
                     last_par = phase;
                     if (++stage == (uint32_t)nst) { stage = 0; phase ^= 1u; }
@@ -1229,8 +1197,6 @@ tc_lagmajor_kernel(const __grid_constant__ CUtensorMap tmap, const uint32_t* __r
                      "r"(TMEM_COLS)
                      : "memory");
     }
-    // the peer no longer writes into this CTA's stages or arrives on its barriers
-    if constexpr (CL == 2) cluster_sync_all();
 }
 
 // Lag-major tiles on CTA pairs with the 2-SM MMA (tcgen05.mma.cta_group::2, M = 256):
@@ -1542,13 +1508,12 @@ pnce_status launch_lagmajor(const pnce_handle* h, const pnce_pilot* pilot, long 
     prm.err = h->status_dev;
     prm.ext_words = pilot->ext_words;
     prm.drop_first_arrive = 0;
-    // CTA pairs when the lag tiles pair up: by default with the 2-SM MMA, each CTA loading
-    // half of the rows; PNCE_TC_LAGMAJOR_CL=2 pairs that share 256-row stages by multicast,
-    // =1 single CTAs (to compare the three)
+    // CTA pairs with the 2-SM MMA, each CTA loading half of the rows, when the lag tiles
+    // pair up; single CTAs otherwise, or with PNCE_TC_LAGMAJOR_CL=1 (to compare the two)
     const char* cl_env = getenv("PNCE_TC_LAGMAJOR_CL");
     const bool pairable = njt % 2 == 0 && njt / 2 <= h->num_sms / 2;
     const int cl = pairable && !(cl_env && cl_env[0] == '1') ? 2 : 1;
-    const bool mma2 = cl == 2 && !(cl_env && cl_env[0] == '2');
+    const bool mma2 = cl == 2;
     // every CTA keeps one lag block: the number of work units (CTAs, or pairs) in flight is
     // a multiple of the lag groups, and at most the number of units of work
     const long long groups = njt / cl;
@@ -1609,10 +1574,8 @@ pnce_status launch_lagmajor(const pnce_handle* h, const pnce_pilot* pilot, long 
                                         pilot->ext_bits_dev, factors, H, prm, 2)
                         : launch_kernel(tc_lagmajor_pair_kernel<DT, 1>, grid, smem, s, pdl, map,
                                         pilot->ext_bits_dev, factors, H, prm, 2);
-    return cl == 2 ? launch_kernel(tc_lagmajor_kernel<DT, 2>, grid, smem, s, pdl, map,
-                                   pilot->ext_bits_dev, factors, H, prm, 2)
-                   : launch_kernel(tc_lagmajor_kernel<DT, 1>, grid, smem, s, pdl, map,
-                                   pilot->ext_bits_dev, factors, H, prm);
+    return launch_kernel(tc_lagmajor_kernel<DT>, grid, smem, s, pdl, map, pilot->ext_bits_dev,
+                         factors, H, prm);
 }
 
 template <int DT>

@@ -82,9 +82,9 @@ def test_layout_rejects_aliasing():
 @pytest.mark.parametrize("dtype", ["fp16", "bf16", "e4m3", "tf32"])
 def test_spread_kernels_agree(dtype, monkeypatch):
     # the even-spread tiles of 128 lags or fewer go to the lag-major kernel (CTA pairs on
-    # the 2-SM MMA, pairs that share each stage by multicast, or single CTAs); every form
-    # gives the same bits as the lag-column kernel, across several row blocks, a ragged
-    # antenna count and an odd number of lag tiles (no pairs)
+    # the 2-SM MMA, or single CTAs); every form gives the same bits as the lag-column
+    # kernel, across several row blocks, a ragged antenna count and an odd number of lag
+    # tiles (no pairs)
     import paper_2206_05506_gb300 as pk
     dev = torch.device("cuda", 0)
     for (r, M, K, L, cp, F) in [(11, 37, 4, 128, 0, 5), (11, 16, 6, 100, 0, 9),
@@ -93,13 +93,13 @@ def test_spread_kernels_agree(dtype, monkeypatch):
         pilot = pk.Pilot(bits, device=dev)
         Yd = torch.from_numpy(Y).to(dev)
         outs = []
-        for lm, cl in (("0", "2"), ("1", "1"), ("1", "2"), ("1", "m")):
+        for lm, cl in (("0", ""), ("1", "1"), ("1", "")):
             monkeypatch.setenv("PNCE_TC_LAGMAJOR", lm)
             monkeypatch.setenv("PNCE_TC_LAGMAJOR_CL", cl)
             outs.append(pk.estimate(Yd, pilot, K, L, dtype=dtype, cp_len=cp,
                                     shift_rule="spread"))
         assert pk.get_status(dev) == 0
-        for i in (1, 2, 3):
+        for i in (1, 2):
             assert torch.equal(outs[0], outs[i]), (r, M, K, L, i)
         ref = O.estimate_general(Y, bits, K, L, cp_len=cp, shifts=sh)
-        assert O.nmse(outs[3].cpu().numpy(), ref) <= TOL[dtype]
+        assert O.nmse(outs[2].cpu().numpy(), ref) <= TOL[dtype]
