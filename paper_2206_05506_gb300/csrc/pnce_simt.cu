@@ -201,57 +201,30 @@ __host__ __device__ constexpr size_t win_bytes(int nred) {
     return ((size_t)win_len(nred) + (size_t)win_len(nred) / 32 + 1) * sizeof(float);
 }
 
-template <int MODE, int RA>
-__global__ void __launch_bounds__(256, 2)
-simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ preal,
-                      const float2* __restrict__ Y, long long y_stride, long long A,
-                      int N /* reduction length */, const pnce::LagMap lags, int nmod,
-                      int num_jt, long long groups, float invN, float2* __restrict__ H) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    WSmem<RA>& sm = *reinterpret_cast<WSmem<RA>*>(smem_raw);
-    float* E = reinterpret_cast<float*>(smem_raw + sizeof(WSmem<RA>));
-
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long long bid = blockIdx.x;
-    long long j0;
-    int col0, valid;
-    pnce::lag_tile(lags, TJ, bid % num_jt, j0, col0, valid);
-    const long long g = bid / num_jt, gbase = A / groups, grem = A % groups;
-    const long long a0 = g * gbase + (g < grem ? g : grem);
-    const int rows = (int)(gbase + (g < grem ? 1 : 0));
+// The rows of one warp: NR (<= RA) received rows from row r0 of the group, the chunks of
+// the reduction double-buffered in the warp's own shared buffers.  Every output is summed
+// over n in the same order whatever NR, so results do not depend on the row split.
+template <int MODE, int RA, int NR>
+__device__ __forceinline__ void warp_rows(WSmem<RA>& sm, const float* __restrict__ E,
+                                          const float2* __restrict__ Y, long long y_stride,
+                                          long long a_first, int N, const pnce::LagMap& lags,
+                                          int col0, int valid, float invN,
+                                          float2* __restrict__ H, int warp, int lane) {
     const int nchunks = (N + NC - 1) / NC;
-    const long long eoff = j0 + TJ - 1;
-
-    {   // the whole pilot window, once
-        const int elen = win_len(N);
-        long long q0 = ((long long)tid - eoff) % nmod;
-        if (q0 < 0) q0 += nmod;
-        int q = (int)q0;
-        const int step = 256 % nmod;
-        for (int t = tid; t < elen; t += 256) {
-            E[epos(t)] = pilot_value<MODE>(bits, preal, q, nmod);
-            q += step;
-            if (q >= nmod) q -= nmod;
-        }
-    }
-    __syncthreads();
-    if (warp * RA >= rows) return;             // no block-wide barrier below
-
     auto stage = [&](int c, int buf) {
         const int n0 = c * NC;
-        for (int i = lane; i < RA * NC; i += 32) {
+        for (int i = lane; i < NR * NC; i += 32) {
             const int aa = i / NC, nn = i % NC;
-            const int r = warp * RA + aa;
-            const bool ok = (r < rows) && (n0 + nn < N);
-            const float2* src = ok ? (Y + (a0 + r) * y_stride + n0 + nn) : Y;
+            const bool ok = n0 + nn < N;
+            const float2* src = ok ? (Y + (a_first + aa) * y_stride + n0 + nn) : Y;
             cp_async8(&sm.y[warp][buf][aa][nn], src, ok);
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
 
-    float2 acc[RA][RJ];
+    float2 acc[NR][RJ];
 #pragma unroll
-    for (int i = 0; i < RA; ++i)
+    for (int i = 0; i < NR; ++i)
 #pragma unroll
         for (int r = 0; r < RJ; ++r) acc[i][r] = make_float2(0.f, 0.f);
     const int base = TJ - 1 - RJ * lane;
@@ -278,9 +251,9 @@ simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict
             for (int i = 0; i < 8; ++i) nw[i] = E[epos(cb + 8 * s + 8 + i)];
 #pragma unroll
             for (int u2 = 0; u2 < 8; u2 += 2) {
-                float4 yy[RA];
+                float4 yy[NR];
 #pragma unroll
-                for (int i = 0; i < RA; ++i)
+                for (int i = 0; i < NR; ++i)
                     yy[i] = *reinterpret_cast<const float4*>(&sm.y[warp][buf][i][8 * s + u2]);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
@@ -289,7 +262,7 @@ simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict
                     for (int r = 0; r < RJ; ++r) {
                         const float pv = w[u - r + 7];
 #pragma unroll
-                        for (int i = 0; i < RA; ++i) {
+                        for (int i = 0; i < NR; ++i) {
                             const float yx = h ? yy[i].z : yy[i].x, yi = h ? yy[i].w : yy[i].y;
                             acc[i][r] = __ffma2_rn(make_float2(pv, pv), make_float2(yx, yi),
                                                    acc[i][r]);
@@ -306,15 +279,71 @@ simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict
     }
 
 #pragma unroll
-    for (int i = 0; i < RA; ++i) {
-        if (warp * RA + i >= rows) continue;
-        const long long a = a0 + warp * RA + i;
-        float2* hrow = H + a * lags.ldH + col0;
+    for (int i = 0; i < NR; ++i) {
+        float2* hrow = H + (a_first + i) * lags.ldH + col0;
 #pragma unroll
         for (int r = 0; r < RJ; ++r) {
             const int j = RJ * lane + r;
             if (j < valid) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
         }
+    }
+}
+
+template <int MODE, int RA>
+__global__ void __launch_bounds__(256, 2)
+simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ preal,
+                      const float2* __restrict__ Y, long long y_stride, long long A,
+                      int N /* reduction length */, const pnce::LagMap lags, int nmod,
+                      int num_jt, long long groups, float invN, float2* __restrict__ H) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    WSmem<RA>& sm = *reinterpret_cast<WSmem<RA>*>(smem_raw);
+    float* E = reinterpret_cast<float*>(smem_raw + sizeof(WSmem<RA>));
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long bid = blockIdx.x;
+    long long j0;
+    int col0, valid;
+    pnce::lag_tile(lags, TJ, bid % num_jt, j0, col0, valid);
+    const long long g = bid / num_jt, gbase = A / groups, grem = A % groups;
+    const long long a0 = g * gbase + (g < grem ? g : grem);
+    const int rows = (int)(gbase + (g < grem ? 1 : 0));     // <= WARPS * RA
+    const long long eoff = j0 + TJ - 1;
+
+    {   // the whole pilot window, once
+        const int elen = win_len(N);
+        long long q0 = ((long long)tid - eoff) % nmod;
+        if (q0 < 0) q0 += nmod;
+        int q = (int)q0;
+        const int step = 256 % nmod;
+        for (int t = tid; t < elen; t += 256) {
+            E[epos(t)] = pilot_value<MODE>(bits, preal, q, nmod);
+            q += step;
+            if (q >= nmod) q -= nmod;
+        }
+    }
+    __syncthreads();
+    // The group's rows spread over the warps as evenly as possible (rows / WARPS or one
+    // more each), so that the four SM sub-partitions, which take warps w, w + 4 of each
+    // block, carry nearly the same number of rows (27 rows as 4+4+4+3+3+3+3+3 rather than
+    // six warps of 4, one of 3 computed as 4, and one idle).  No block-wide barrier below.
+    const int rbase = rows / WARPS, rextra = rows % WARPS;
+    const int nrw = rbase + (warp < rextra ? 1 : 0);
+    const long long a_first = a0 + (long long)warp * rbase + (warp < rextra ? warp : rextra);
+    if (nrw == 4) {
+        if constexpr (RA >= 4)
+            warp_rows<MODE, RA, 4>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
+                                   warp, lane);
+    } else if (nrw == 3) {
+        if constexpr (RA >= 3)
+            warp_rows<MODE, RA, 3>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
+                                   warp, lane);
+    } else if (nrw == 2) {
+        if constexpr (RA >= 2)
+            warp_rows<MODE, RA, 2>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
+                                   warp, lane);
+    } else if (nrw == 1) {
+        warp_rows<MODE, RA, 1>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H, warp,
+                               lane);
     }
 }
 
