@@ -232,17 +232,19 @@ def oracle_references() -> dict:
             "paper_scale": O.estimate(pY, pbits, ps.K, ps.L)}
 
 
-SWEEP_RATES_HZ = (10000.0, 20000.0, 40000.0, 80000.0, 160000.0)
+SWEEP_RATES_HZ = (10000.0, 20000.0, 40000.0, 80000.0, 120000.0, 160000.0)
 
 
 def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
                 sweep_rates=SWEEP_RATES_HZ, sweep_seconds: float = 2.0):
     """Poisson request stream (uneven M, N, K, L) through the continuous-batching server,
-    tensor cores (fp16) and the plain FP32 SIMT path on the same trace.  refs: the oracle's
-    results per payload (from oracle_references) for the spot check, or None.  Then, per
-    path, an arrival-rate sweep (shorter traces): p50 / p99 latency and delivered frames/s
-    at each offered rate, and the knee -- the highest offered rate still delivered (>= 95 %)
-    with p99 within 4x of the lowest rate's."""
+    tensor cores (fp16) and the plain FP32 SIMT path on the same trace, each through the
+    library's native serving loop (the reported figures) and through the Python loop with
+    the same rules (`python_loop`).  refs: the oracle's results per payload (from
+    oracle_references) for the spot check, or None.  Then, per path and loop, an
+    arrival-rate sweep (shorter traces): p50 / p99 latency and delivered frames/s at each
+    offered rate, and the knee -- the highest offered rate still delivered (>= 95 %) with
+    p99 within 4x of the lowest rate's."""
     import torch
 
     from paper_2206_05506_gb300 import serve
@@ -289,14 +291,12 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
 
     res = {"rate_hz": rate_hz, "seconds": seconds, "requests": len(specs)}
     sweep_specs = {rate: trace(rate, sweep_seconds, 1 + i) for i, rate in enumerate(sweep_rates)}
-    for dtype, name in (("fp16", "fp16_tensor_core"), ("fp32", "fp32_simt")):
-        eng = serve.GpuEngine(S.pilot_bits, device=dev, dtype=dtype, slots=4)
-        eng.prepare([255, 511, 1023, 2047])
+    def measure(run):
+        """The main trace (with the oracle spot check) and the rate sweep through `run`."""
         reqs = requests(specs, True)
-        serve.Server(eng).run([serve.Request(-1, 0.0, r.M, r.N, r.K, r.L, r.y_addr, r.h_addr)
-                               for r in reqs[:200]])            # warm the path
-        srv = serve.Server(eng, mem_cap_bytes=40e9)
-        st = srv.run(reqs)
+        run([serve.Request(-1, 0.0, r.M, r.N, r.K, r.L, r.y_addr, r.h_addr)
+             for r in reqs[:200]])                          # warm the path
+        st = run(reqs)
         # accuracy of the sampled requests against the oracle's results
         errs = []
         for r in reqs if refs is not None else []:
@@ -311,7 +311,7 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
                             "nmse_median": float(np.median(errs)) if errs else None}
         sweep = []
         for rate in sweep_rates:
-            sst = serve.Server(eng, mem_cap_bytes=40e9).run(requests(sweep_specs[rate], False))
+            sst = run(requests(sweep_specs[rate], False))
             sweep.append({"offered_hz": rate, "delivered_frames_per_s": sst["frames_per_s"],
                           "p50_ms": sst["p50_ms"], "p99_ms": sst["p99_ms"],
                           "max_ms": sst["max_ms"], "mean_batch_rows": sst["mean_batch_rows"],
@@ -324,6 +324,19 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
                 knee = row["offered_hz"]
         st["rate_sweep"] = {"seconds_per_rate": sweep_seconds, "rows": sweep,
                             "knee_offered_hz": knee}
+        return st
+
+    res["loop"] = ("native: the scheduling loop in the library (pnce_server_run); "
+                   "python_loop: the same rules in serve.Server")
+    for dtype, name in (("fp16", "fp16_tensor_core"), ("fp32", "fp32_simt")):
+        nat = serve.NativeServer(S.pilot_bits, device=dev, dtype=dtype, slots=4,
+                                 mem_cap_bytes=40e9)
+        nat.prepare([255, 511, 1023, 2047])
+        st = measure(nat.run)
+        del nat
+        eng = serve.GpuEngine(S.pilot_bits, device=dev, dtype=dtype, slots=4)
+        eng.prepare([255, 511, 1023, 2047])
+        st["python_loop"] = measure(lambda rq: serve.Server(eng, mem_cap_bytes=40e9).run(rq))
         res[name] = st
         del eng
         torch.cuda.empty_cache()

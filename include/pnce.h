@@ -298,6 +298,68 @@ pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
                                   int dtype, void* workspace_dev, size_t workspace_bytes,
                                   void* stream);
 
+/* Native serving loop (continuous batching of uneven requests, built on
+ * pnce_estimate_grouped; the paper has no counterpart).  A run replays a trace open loop:
+ * request i is submitted t_arrival seconds after the run starts (t_arrival non-decreasing).
+ * Admission: in arrival order while the footprint of admitted, unfinished requests stays
+ * within mem_cap_bytes (a request is admitted regardless when nothing is in flight; the
+ * footprint of a request is M * (8 N + 2 e pitch(N) + 8 kl_class) bytes, e the operand
+ * element bytes of dtype (0 for FP32, 2 for PNCE_AUTO), pitch(N) = N rounded up to 64).
+ * Admitted requests wait in buckets keyed by (N, kl_class), kl_class the smallest of
+ * 64, 256, 1024 that holds K*L, capped at N (above 1024: K*L rounded up to 1024, capped
+ * at N).  Whenever one of the
+ * `slots` streams is free the bucket whose oldest request arrived first (ties: smaller N,
+ * then smaller class) is launched as one grouped batch, packing its requests in order while
+ * their antennas fit max_batch_rows (always at least one).  A batch runs as one replay of a
+ * CUDA graph captured per (slot, N, class, capacity), capacity the smallest of 64, 256,
+ * 1024, 4096 antennas that holds it (larger: a multiple of 4096).  Completion = its event,
+ * polled in launch order.  The run busy-polls on the calling thread; a server is used by
+ * one thread at a time.
+ *
+ * pnce_server_create: dtype as pnce_estimate_grouped (PNCE_AUTO resolved per bucket);
+ *   1 <= slots <= 64.  Creates the streams and events; the caller keeps h alive.
+ * pnce_server_add_pilot: the pilot for one PN length N (not owned: keep it alive while
+ *   the server runs).  A request whose N has no pilot fails (status PNCE_EINVAL).
+ * pnce_server_prepare: captures the graphs of one (N, kl_class, capacity) shape on every
+ *   slot ahead of a run (a run captures missing shapes when it first needs them, inside
+ *   its timed loop).  Allocates the shape's workspace and page-locked descriptor table.
+ * pnce_server_run: reqs[n] in host memory; each request's Y (complex64 [M][N]) and H
+ *   (complex64 [M][K*L]) as in pnce_req_desc.  out[n]: per request the admission, launch
+ *   and completion times (seconds from the start of the run), the batch index and a
+ *   status (PNCE_OK, or the status that failed its batch: PNCE_ECUDA for a launch or an
+ *   event error, PNCE_EINVAL for a missing pilot, PNCE_ENOMEM for a shape that could not be
+ *   allocated).  Returns PNCE_EINVAL for invalid arguments (nothing run), else, after every
+ *   batch completed, the status latched on the device by the run's kernels (PNCE_OK when
+ *   none; otherwise some results may be wrong).
+ * pnce_sched_simulate: the same scheduling rules on a virtual clock, no GPU: the clock
+ *   advances by clock_dt at every pass of the loop, a batch of r antennas completes
+ *   base_s + per_row_s * r seconds after its launch, a request's footprint is
+ *   M * row_bytes.  Fills out[n] and *batches as pnce_server_run does.
+ */
+typedef struct pnce_server pnce_server;
+typedef struct {
+    const void* Y;          /* complex64 [M][N] */
+    void* H;                /* complex64 [M][K*L] */
+    int M, N, K, L;
+    double t_arrival;       /* seconds from the start of the run */
+} pnce_serve_req;
+typedef struct {
+    double t_admit, t_launch, t_done;   /* seconds from the start of the run */
+    int batch;
+    int status;
+} pnce_serve_out;
+pnce_status pnce_server_create(pnce_handle* h, int dtype, int slots, double mem_cap_bytes,
+                               int max_batch_rows, pnce_server** out);
+pnce_status pnce_server_destroy(pnce_server* server);
+pnce_status pnce_server_add_pilot(pnce_server* server, const pnce_pilot* pilot);
+pnce_status pnce_server_prepare(pnce_server* server, int N, int kl_class, int capacity);
+pnce_status pnce_server_run(pnce_server* server, const pnce_serve_req* reqs, int n,
+                            pnce_serve_out* out, int* batches);
+pnce_status pnce_sched_simulate(const pnce_serve_req* reqs, int n, int slots,
+                                double mem_cap_bytes, int max_batch_rows, double row_bytes,
+                                double base_s, double per_row_s, double clock_dt,
+                                pnce_serve_out* out, int* batches);
+
 pnce_status pnce_gather_rows(const uint64_t* src_rows, int rows, int nelem, void* dst_dev,
                              long long dst_pitch, void* stream);
 pnce_status pnce_scatter_rows(const void* src_dev, long long src_pitch, const uint64_t* dst_rows,

@@ -37,6 +37,18 @@ class FrameOpts(C.Structure):
     """pnce_frame_opts"""
     _fields_ = [("cp_len", C.c_int), ("shift_rule", C.c_int)]
 
+
+class ServeReq(C.Structure):
+    """pnce_serve_req: one request of a native serving run."""
+    _fields_ = [("Y", C.c_void_p), ("H", C.c_void_p), ("M", C.c_int), ("N", C.c_int),
+                ("K", C.c_int), ("L", C.c_int), ("t_arrival", C.c_double)]
+
+
+class ServeOut(C.Structure):
+    """pnce_serve_out: what a native serving run reports per request."""
+    _fields_ = [("t_admit", C.c_double), ("t_launch", C.c_double), ("t_done", C.c_double),
+                ("batch", C.c_int), ("status", C.c_int)]
+
 _SIGS = {
     "pnce_version": (_i, []),
     "pnce_auto_dtype": (_i, [_i, _i, _i]),
@@ -69,6 +81,13 @@ _SIGS = {
     "pnce_trace_read": (_i, [_vp, _vp, _vp, _i, C.POINTER(C.c_int)]),
     "pnce_gather_rows": (_i, [_vp, _i, _i, _vp, C.c_longlong, _vp]),
     "pnce_scatter_rows": (_i, [_vp, C.c_longlong, _vp, _vp, _i, _vp]),
+    "pnce_server_create": (_i, [_vp, _i, _i, C.c_double, _i, C.POINTER(_vp)]),
+    "pnce_server_destroy": (_i, [_vp]),
+    "pnce_server_add_pilot": (_i, [_vp, _vp]),
+    "pnce_server_prepare": (_i, [_vp, _i, _i, _i]),
+    "pnce_server_run": (_i, [_vp, _vp, _i, _vp, C.POINTER(_i)]),
+    "pnce_sched_simulate": (_i, [_vp, _i, _i, C.c_double, _i, C.c_double, C.c_double,
+                                 C.c_double, C.c_double, _vp, C.POINTER(_i)]),
 }
 
 

@@ -21,7 +21,7 @@ LIB_NAME = "libpnce.so"
 LIB_PATH = os.path.join(PKG_DIR, LIB_NAME)
 
 SOURCES = ["pnce_api.cu", "pnce_simt.cu", "pnce_quant.cu", "pnce_tc.cu", "pnce_adjoint.cu",
-           "pnce_static.cu", "pnce_serve.cu", "pnce_fmt.cu"]
+           "pnce_static.cu", "pnce_serve.cu", "pnce_fmt.cu", "pnce_server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

@@ -1,0 +1,499 @@
+// Native continuous-batching server: the scheduling loop of a serving run in C++, so that
+// the host side of a batch (descriptor table, graph launch, completion event) costs a few
+// microseconds instead of the tens that a Python loop spends per batch.
+//
+// Scheduling (the same rules as paper_2206_05506_gb300/serve.py's Server, decision for
+// decision -- pnce_sched_simulate runs them on a virtual clock so that the two can be
+// compared exactly): requests are admitted in arrival order while the bytes of admitted,
+// unfinished work stay under a cap (a request is admitted regardless when nothing is in
+// flight); admitted requests wait in buckets keyed by (N, lag class); whenever a stream
+// slot is free, the bucket whose oldest request arrived first (ties: the smaller key) is
+// launched, packing its requests in order while their antennas fit max_batch_rows (at
+// least one request per batch); completions are polled in launch order.
+//
+// Execution: one CUDA graph per (slot, N, lag class, capacity) captured around one
+// pnce_estimate_grouped call, whose descriptor table sits in page-locked host memory and
+// is rewritten before each replay; one stream and one completion event per slot.  A table
+// is rewritten only after its slot's previous batch completed.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <deque>
+#include <map>
+#include <memory>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+#include "pnce_internal.h"
+
+namespace {
+
+// lag classes and batch capacities (antennas) of the serving shapes
+constexpr int kKlClasses[3] = {64, 256, 1024};
+constexpr int kCapacities[4] = {64, 256, 1024, 4096};
+
+int kl_class(int KL, int N) {
+    for (int c : kKlClasses)
+        if (c >= KL) return std::min(c, N);
+    return std::min((KL + 1023) / 1024 * 1024, N);
+}
+
+int capacity_for(long long rows) {
+    for (int c : kCapacities)
+        if (c >= rows) return c;
+    return (int)((rows + 4095) / 4096 * 4096);
+}
+
+struct ReqState {
+    double nbytes = 0.0;
+    int klc = 0;
+};
+
+// The scheduling rules over an executor E:
+//   double E::footprint(const pnce_serve_req&)
+//   bool   E::launch(int slot, int N, int klc, const std::vector<int>& ids, long long rows,
+//                    int* status)                      -- false: the batch failed to start
+//   int    E::done(int slot)                           -- 1 done, 0 running, < 0 failed
+template <class E>
+class Scheduler {
+  public:
+    Scheduler(E& ex, const pnce_serve_req* reqs, int n, pnce_serve_out* out, int slots,
+              double mem_cap, int max_rows)
+        : ex_(ex), reqs_(reqs), n_(n), out_(out), cap_(mem_cap), max_rows_(max_rows) {
+        for (int s = slots - 1; s >= 0; --s) free_.push_back(s);
+        st_.resize((size_t)n);
+        for (int i = 0; i < n; ++i) {
+            out_[i] = pnce_serve_out{-1.0, -1.0, -1.0, -1, 0};
+            st_[(size_t)i].klc = kl_class(reqs_[i].K * reqs_[i].L, reqs_[i].N);
+        }
+    }
+
+    // one pass: submit the arrivals up to `now`, then complete, admit and launch
+    void step(double now) {
+        while (next_ < n_ && reqs_[next_].t_arrival <= now) {
+            st_[(size_t)next_].nbytes = ex_.footprint(reqs_[next_]);
+            pending_.push_back(next_++);
+        }
+        complete(now);
+        admit(now);
+        launch(now);
+    }
+
+    bool finished() const {
+        if (next_ < n_ || !pending_.empty() || !busy_.empty()) return false;
+        for (const auto& b : buckets_)
+            if (!b.second.empty()) return false;
+        return true;
+    }
+
+    int batches() const { return batches_; }
+    double peak_inflight() const { return peak_; }
+
+  private:
+    struct Busy {
+        int slot;
+        std::vector<int> ids;
+    };
+
+    void release(const std::vector<int>& ids, double now, int status) {
+        for (int i : ids) {
+            out_[i].t_done = now;
+            out_[i].status = status;
+            inflight_ -= st_[(size_t)i].nbytes;
+        }
+    }
+
+    void complete(double now) {
+        std::vector<Busy> still;
+        for (auto& b : busy_) {
+            const int d = ex_.done(b.slot);
+            if (d == 0) {
+                still.push_back(std::move(b));
+                continue;
+            }
+            release(b.ids, now, d > 0 ? (int)PNCE_OK : (int)PNCE_ECUDA);
+            free_.push_back(b.slot);
+        }
+        busy_.swap(still);
+    }
+
+    void admit(double now) {
+        while (!pending_.empty()) {
+            const int i = pending_.front();
+            const double nb = st_[(size_t)i].nbytes;
+            if (inflight_ + nb > cap_ && inflight_ > 0) break;   // wait for memory
+            pending_.pop_front();
+            inflight_ += nb;
+            peak_ = std::max(peak_, inflight_);
+            out_[i].t_admit = now;
+            buckets_[{reqs_[i].N, st_[(size_t)i].klc}].push_back(i);
+        }
+    }
+
+    void launch(double now) {
+        while (!free_.empty()) {
+            // the bucket whose head arrived first; ties go to the smaller (N, klc) key
+            std::deque<int>* q = nullptr;
+            std::pair<int, int> key{0, 0};
+            double best = 0.0;
+            for (auto& b : buckets_) {
+                if (b.second.empty()) continue;
+                const double t = reqs_[b.second.front()].t_arrival;
+                if (!q || t < best) {
+                    q = &b.second;
+                    key = b.first;
+                    best = t;
+                }
+            }
+            if (!q) return;
+            std::vector<int> ids;
+            long long rows = 0;
+            while (!q->empty() && rows + reqs_[q->front()].M <= max_rows_) {
+                rows += reqs_[q->front()].M;
+                ids.push_back(q->front());
+                q->pop_front();
+            }
+            if (ids.empty()) {                     // a single request above max_rows
+                ids.push_back(q->front());
+                rows = reqs_[q->front()].M;
+                q->pop_front();
+            }
+            const int slot = free_.back();
+            free_.pop_back();
+            for (int i : ids) {
+                out_[i].t_launch = now;
+                out_[i].batch = batches_;
+            }
+            int status = PNCE_OK;
+            if (!ex_.launch(slot, key.first, key.second, ids, rows, &status)) {
+                release(ids, now, status == PNCE_OK ? (int)PNCE_ECUDA : status);
+                free_.push_back(slot);
+                continue;
+            }
+            busy_.push_back(Busy{slot, std::move(ids)});
+            ++batches_;
+        }
+    }
+
+    E& ex_;
+    const pnce_serve_req* reqs_;
+    int n_;
+    pnce_serve_out* out_;
+    double cap_;
+    int max_rows_;
+    std::vector<ReqState> st_;
+    int next_ = 0;
+    std::deque<int> pending_;
+    std::map<std::pair<int, int>, std::deque<int>> buckets_;
+    std::vector<int> free_;
+    std::vector<Busy> busy_;
+    double inflight_ = 0.0, peak_ = 0.0;
+    int batches_ = 0;
+};
+
+// Virtual time (no GPU): a batch of r rows takes base + per_row * r seconds; a request's
+// footprint is M * row_bytes; the clock advances by dt at every pass of the loop.
+struct SimExec {
+    double* t;
+    double base, per_row, row_bytes;
+    std::vector<double> end;
+    std::vector<char> running;
+    double footprint(const pnce_serve_req& r) const { return (double)r.M * row_bytes; }
+    bool launch(int slot, int, int, const std::vector<int>&, long long rows, int*) {
+        end[(size_t)slot] = *t + base + per_row * (double)rows;
+        running[(size_t)slot] = 1;
+        return true;
+    }
+    int done(int slot) {
+        if (running[(size_t)slot] && *t >= end[(size_t)slot]) running[(size_t)slot] = 0;
+        return running[(size_t)slot] ? 0 : 1;
+    }
+};
+
+bool serve_args_ok(const pnce_serve_req* reqs, int n, const pnce_serve_out* out, int slots,
+                   double mem_cap, int max_rows) {
+    if (n < 0 || (n > 0 && (!reqs || !out)) || slots < 1 || slots > 64 || max_rows < 1 ||
+        !(mem_cap > 0.0))
+        return false;
+    for (int i = 0; i < n; ++i) {
+        const pnce_serve_req& r = reqs[i];
+        if (r.M < 1 || r.N < 2 || r.K < 1 || r.L < 1 || (long long)r.K * r.L > r.N ||
+            !std::isfinite(r.t_arrival) || (i > 0 && r.t_arrival < reqs[i - 1].t_arrival))
+            return false;
+    }
+    return true;
+}
+
+}  // namespace
+
+extern "C" pnce_status pnce_sched_simulate(const pnce_serve_req* reqs, int n, int slots,
+                                           double mem_cap, int max_batch_rows, double row_bytes,
+                                           double base_s, double per_row_s, double clock_dt,
+                                           pnce_serve_out* out, int* batches) {
+    if (!serve_args_ok(reqs, n, out, slots, mem_cap, max_batch_rows) || !(clock_dt > 0.0) ||
+        !(base_s >= 0.0) || !(per_row_s >= 0.0) || !(row_bytes >= 0.0))
+        return PNCE_EINVAL;
+    double t = 0.0;
+    SimExec ex{&t, base_s, per_row_s, row_bytes, std::vector<double>((size_t)slots, 0.0),
+               std::vector<char>((size_t)slots, 0)};
+    Scheduler<SimExec> sch(ex, reqs, n, out, slots, mem_cap, max_batch_rows);
+    while (!sch.finished()) {
+        t += clock_dt;
+        sch.step(t);
+    }
+    if (batches) *batches = sch.batches();
+    return PNCE_OK;
+}
+
+namespace {
+
+// One batch shape on one slot: its workspace, its page-locked descriptor table and the
+// graph captured around pnce_estimate_grouped over them.
+struct ServeShape {
+    int N = 0, klc = 0, cap = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    pnce_req_desc* desc = nullptr;
+    int used = 0;                            // descriptors written by the last batch
+    cudaGraphExec_t exec = nullptr;
+};
+
+}  // namespace
+
+struct pnce_server {
+    pnce_handle* h = nullptr;
+    int dtype = PNCE_FP16;
+    int slots = 0;
+    double mem_cap = 0.0;
+    int max_rows = 0;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    std::map<int, const pnce_pilot*> pilots;                 // by N; not owned
+    std::map<std::tuple<int, int, int, int>, std::unique_ptr<ServeShape>> shapes;
+};
+
+namespace {
+
+void free_shape(ServeShape* s) {
+    if (s->exec) cudaGraphExecDestroy(s->exec);
+    if (s->ws) cudaFree(s->ws);
+    if (s->desc) cudaFreeHost(s->desc);
+    s->exec = nullptr;
+    s->ws = nullptr;
+    s->desc = nullptr;
+}
+
+// Create and capture shape (slot, N, klc, cap), or return the existing one.
+pnce_status get_shape(pnce_server* sv, int slot, int N, int klc, int cap, ServeShape** out) {
+    const auto key = std::make_tuple(slot, N, klc, cap);
+    auto it = sv->shapes.find(key);
+    if (it != sv->shapes.end()) {
+        *out = it->second.get();
+        return PNCE_OK;
+    }
+    auto pit = sv->pilots.find(N);
+    if (pit == sv->pilots.end()) return PNCE_EINVAL;
+    const pnce_pilot* pilot = pit->second;
+    auto sh = std::make_unique<ServeShape>();
+    sh->N = N;
+    sh->klc = klc;
+    sh->cap = cap;
+    sh->ws_bytes = pnce_grouped_workspace_size(cap, N, klc, sv->dtype);
+    if (sh->ws_bytes == 0) return PNCE_EINVAL;
+    if (cudaMalloc(&sh->ws, sh->ws_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return PNCE_ENOMEM;
+    }
+    if (cudaHostAlloc(reinterpret_cast<void**>(&sh->desc), sizeof(pnce_req_desc) * (size_t)cap,
+                      cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        free_shape(sh.get());
+        return PNCE_ENOMEM;
+    }
+    std::fill(sh->desc, sh->desc + cap, pnce_req_desc{nullptr, nullptr, 0, 0, 0, 0});
+    cudaStream_t s = sv->streams[(size_t)slot];
+    // an eager run first (it sets the kernels' attributes), then the capture
+    pnce_status st = pnce_estimate_grouped(sv->h, pilot, sh->desc, cap, cap, klc, sv->dtype,
+                                           sh->ws, sh->ws_bytes, s);
+    if (st == PNCE_OK && cudaStreamSynchronize(s) != cudaSuccess) st = PNCE_ECUDA;
+    if (st != PNCE_OK) {
+        free_shape(sh.get());
+        return st;
+    }
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        free_shape(sh.get());
+        return PNCE_ECUDA;
+    }
+    st = pnce_estimate_grouped(sv->h, pilot, sh->desc, cap, cap, klc, sv->dtype, sh->ws,
+                               sh->ws_bytes, s);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(s, &g);
+    if (st == PNCE_OK && (ce != cudaSuccess || !g)) st = PNCE_ECUDA;
+    if (st == PNCE_OK && cudaGraphInstantiate(&sh->exec, g, 0) != cudaSuccess) st = PNCE_ECUDA;
+    if (g) cudaGraphDestroy(g);
+    if (st != PNCE_OK) {
+        cudaGetLastError();
+        free_shape(sh.get());
+        return st;
+    }
+    *out = sh.get();
+    sv->shapes.emplace(key, std::move(sh));
+    return PNCE_OK;
+}
+
+// Executes batches on the GPU for the scheduler: footprint as the Python engine counts it
+// (received rows, operand rows, result rows of the batch buffers).
+struct CudaExec {
+    pnce_server* sv;
+    int elt;
+    double footprint(const pnce_serve_req& r) const {
+        const double pitch = (double)((r.N + 63) / 64 * 64);
+        return (double)r.M * (8.0 * r.N + 2.0 * elt * pitch + 8.0 * kl_class(r.K * r.L, r.N));
+    }
+    bool launch(int slot, int N, int klc, const std::vector<int>& ids, long long rows,
+                int* status, const pnce_serve_req* reqs) {
+        ServeShape* sh = nullptr;
+        const pnce_status st = get_shape(sv, slot, N, klc, capacity_for(rows), &sh);
+        if (st != PNCE_OK) {
+            *status = st;
+            return false;
+        }
+        int off = 0;
+        const int n = (int)ids.size();
+        for (int k = 0; k < n; ++k) {
+            const pnce_serve_req& r = reqs[ids[(size_t)k]];
+            sh->desc[k] = pnce_req_desc{r.Y, r.H, r.M, r.K, r.L, off};
+            off += r.M;
+        }
+        for (int k = n; k < sh->used; ++k) sh->desc[k].M = 0;    // empty slots
+        sh->used = n;
+        cudaStream_t s = sv->streams[(size_t)slot];
+        if (cudaGraphLaunch(sh->exec, s) != cudaSuccess ||
+            cudaEventRecord(sv->events[(size_t)slot], s) != cudaSuccess) {
+            cudaGetLastError();
+            *status = PNCE_ECUDA;
+            return false;
+        }
+        return true;
+    }
+    int done(int slot) {
+        const cudaError_t e = cudaEventQuery(sv->events[(size_t)slot]);
+        if (e == cudaSuccess) return 1;
+        if (e == cudaErrorNotReady) return 0;
+        cudaGetLastError();
+        return -1;
+    }
+};
+
+// binds the request table to CudaExec's launch (the scheduler passes ids only)
+struct CudaExecBound {
+    CudaExec ex;
+    const pnce_serve_req* reqs;
+    double footprint(const pnce_serve_req& r) const { return ex.footprint(r); }
+    bool launch(int slot, int N, int klc, const std::vector<int>& ids, long long rows,
+                int* status) {
+        return ex.launch(slot, N, klc, ids, rows, status, reqs);
+    }
+    int done(int slot) { return ex.done(slot); }
+};
+
+int operand_elt(int dtype) {
+    switch (dtype) {
+        case PNCE_FP32_SIMT: return 0;
+        case PNCE_TF32: return 4;
+        case PNCE_FP8E4M3: return 1;
+        default: return 2;                   // fp16, bf16, and PNCE_AUTO's upper bound
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+pnce_status pnce_server_create(pnce_handle* h, int dtype, int slots, double mem_cap_bytes,
+                               int max_batch_rows, pnce_server** out) {
+    if (!h || !out || slots < 1 || slots > 64 || !(mem_cap_bytes > 0.0) || max_batch_rows < 1)
+        return PNCE_EINVAL;
+    if (!(dtype == PNCE_FP32_SIMT || dtype == PNCE_TF32 || dtype == PNCE_FP16 ||
+          dtype == PNCE_BF16 || dtype == PNCE_FP8E4M3 || dtype == PNCE_AUTO))
+        return PNCE_EINVAL;
+    *out = nullptr;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PNCE_ECUDA;
+    if (dev != h->device) return PNCE_ESTATE;
+    auto sv = std::make_unique<pnce_server>();
+    sv->h = h;
+    sv->dtype = dtype;
+    sv->slots = slots;
+    sv->mem_cap = mem_cap_bytes;
+    sv->max_rows = max_batch_rows;
+    for (int i = 0; i < slots; ++i) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t e = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            pnce_server_destroy(sv.release());
+            return PNCE_ECUDA;
+        }
+        sv->streams.push_back(s);
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            pnce_server_destroy(sv.release());
+            return PNCE_ECUDA;
+        }
+        sv->events.push_back(e);
+    }
+    *out = sv.release();
+    return PNCE_OK;
+}
+
+pnce_status pnce_server_destroy(pnce_server* sv) {
+    if (!sv) return PNCE_EINVAL;
+    for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
+    for (auto& kv : sv->shapes) free_shape(kv.second.get());
+    for (cudaEvent_t e : sv->events) cudaEventDestroy(e);
+    for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
+    delete sv;
+    return PNCE_OK;
+}
+
+pnce_status pnce_server_add_pilot(pnce_server* sv, const pnce_pilot* pilot) {
+    if (!sv || !pilot) return PNCE_EINVAL;
+    if (pilot->device != sv->h->device) return PNCE_ESTATE;
+    sv->pilots[pilot->N] = pilot;
+    return PNCE_OK;
+}
+
+pnce_status pnce_server_prepare(pnce_server* sv, int N, int kl_class_, int capacity) {
+    if (!sv || capacity < 1 || kl_class_ < 1 || kl_class_ > N) return PNCE_EINVAL;
+    for (int slot = 0; slot < sv->slots; ++slot) {
+        ServeShape* sh = nullptr;
+        const pnce_status st = get_shape(sv, slot, N, kl_class_, capacity, &sh);
+        if (st != PNCE_OK) return st;
+    }
+    return PNCE_OK;
+}
+
+pnce_status pnce_server_run(pnce_server* sv, const pnce_serve_req* reqs, int n,
+                            pnce_serve_out* out, int* batches) {
+    if (!sv || !serve_args_ok(reqs, n, out, sv->slots, sv->mem_cap, sv->max_rows))
+        return PNCE_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!reqs[i].Y || !reqs[i].H) return PNCE_EINVAL;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PNCE_ECUDA;
+    if (dev != sv->h->device) return PNCE_ESTATE;
+    CudaExecBound ex{CudaExec{sv, operand_elt(sv->dtype)}, reqs};
+    Scheduler<CudaExecBound> sch(ex, reqs, n, out, sv->slots, sv->mem_cap, sv->max_rows);
+    using clk = std::chrono::steady_clock;
+    const clk::time_point t0 = clk::now();
+    while (!sch.finished())
+        sch.step(std::chrono::duration<double>(clk::now() - t0).count());
+    if (batches) *batches = sch.batches();
+    // a kernel of these batches may have latched an error (a bounded wait that ran out, an
+    // invalid descriptor): then some results may be wrong, and the run says so
+    for (cudaStream_t s : sv->streams)
+        if (cudaStreamSynchronize(s) != cudaSuccess) return PNCE_ECUDA;
+    return pnce_get_status(sv->h, sv->streams[0]);
+}
+
+}  // extern "C"

@@ -39,7 +39,8 @@ from dataclasses import dataclass
 import numpy as np
 import torch
 
-from . import DTYPES, Pilot, _lib, check, context, estimate_grouped, grouped_workspace_size
+from . import (DTYPES, Pilot, _lib, check, context, estimate_grouped, grouped_workspace_size,
+               lib)
 
 KL_CLASSES = (64, 256, 1024)
 CAPACITIES = (64, 256, 1024, 4096)        # antennas per batch
@@ -335,3 +336,124 @@ class GpuEngine:
         (reads and clears the handle's status word; waits for the device)."""
         torch.cuda.synchronize(self.device)
         check(self.ctx.status(), "serving batches")
+
+
+# Request and result tables of the native loop (pnce_serve_req / pnce_serve_out)
+REQ_DTYPE = np.dtype([("Y", np.uint64), ("H", np.uint64), ("M", np.int32), ("N", np.int32),
+                      ("K", np.int32), ("L", np.int32), ("t_arrival", np.float64)])
+OUT_DTYPE = np.dtype([("t_admit", np.float64), ("t_launch", np.float64),
+                      ("t_done", np.float64), ("batch", np.int32), ("status", np.int32)])
+assert REQ_DTYPE.itemsize == C.sizeof(_lib.ServeReq) and OUT_DTYPE.itemsize == C.sizeof(_lib.ServeOut)
+
+
+def _req_table(requests: list) -> np.ndarray:
+    a = np.empty(len(requests), dtype=REQ_DTYPE)
+    a["Y"] = [r.y_addr for r in requests]
+    a["H"] = [r.h_addr for r in requests]
+    a["M"] = [r.M for r in requests]
+    a["N"] = [r.N for r in requests]
+    a["K"] = [r.K for r in requests]
+    a["L"] = [r.L for r in requests]
+    a["t_arrival"] = [r.t_arrival for r in requests]
+    return a
+
+
+def _native_stats(requests: list, out: np.ndarray, batches: int) -> dict:
+    """Write the run's times into the Request objects and summarise them as Server.stats
+    does."""
+    ok = out["status"] == 0
+    for r, o in zip(requests, out):
+        r.t_admit, r.t_launch, r.t_done = float(o["t_admit"]), float(o["t_launch"]), float(o["t_done"])
+        r.batch = int(o["batch"])
+        r.error = "" if o["status"] == 0 else f"status {int(o['status'])}"
+    if not ok.any():
+        return {"requests": 0, "failed": int((~ok).sum())}
+    t_arr = np.array([r.t_arrival for r in requests])
+    M = np.array([r.M for r in requests], dtype=np.float64)
+    KL = np.array([r.K * r.L for r in requests], dtype=np.float64)
+    lat = (out["t_done"] - t_arr)[ok]
+    span = max(float(out["t_done"][ok].max() - t_arr[ok].min()), 1e-9)
+    launched = out["batch"] >= 0
+    rows = np.bincount(out["batch"][launched], weights=M[launched], minlength=batches)[:batches]
+    return {"requests": int(lat.size), "batches": int(batches),
+            "mean_batch_rows": float(rows.mean()) if batches else 0.0,
+            "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3),
+            "max_ms": float(lat.max() * 1e3),
+            "frames_per_s": lat.size / span, "taps_per_s": float((M * KL)[ok].sum()) / span,
+            "failed": int((~ok).sum())}
+
+
+def simulate(requests: list, slots: int, mem_cap_bytes: float, max_batch_rows: int = 4096,
+             row_bytes: float = 1000.0, base_s: float = 200e-6, per_row_s: float = 0.2e-6,
+             clock_dt: float = 5e-6):
+    """The native loop's scheduling on a virtual clock, no GPU (pnce_sched_simulate):
+    returns (per-request results as OUT_DTYPE, number of batches)."""
+    reqs = _req_table(requests)
+    out = np.empty(len(requests), dtype=OUT_DTYPE)
+    nb = C.c_int(0)
+    check(lib().pnce_sched_simulate(reqs.ctypes.data, len(requests), slots,
+                                         float(mem_cap_bytes), max_batch_rows, float(row_bytes),
+                                         float(base_s), float(per_row_s), float(clock_dt),
+                                         out.ctypes.data, C.byref(nb)), "pnce_sched_simulate")
+    return out, nb.value
+
+
+class NativeServer:
+    """The serving loop run inside the library (pnce_server_*): the scheduling rules of
+    Server, with the host side of each batch -- its descriptor table, the graph launch and
+    the completion event -- in C++.  Requests as for Server; run() replays them open loop
+    on the calling thread and returns the same statistics."""
+
+    def __init__(self, pilot_bits, device=None, dtype: str = "fp16", slots: int = 4,
+                 mem_cap_bytes: float = 40e9, max_batch_rows: int = 4096):
+        self.ctx = context(device)
+        self.device = self.ctx.device
+        self.dtype, self.slots = dtype, slots
+        self._pilot_bits = pilot_bits
+        self._pilots: dict[int, Pilot] = {}
+        p = C.c_void_p()
+        with torch.cuda.device(self.device):
+            check(lib().pnce_server_create(self.ctx.handle, DTYPES[dtype], slots,
+                                                float(mem_cap_bytes), max_batch_rows,
+                                                C.byref(p)), "pnce_server_create")
+        self._s = p
+
+    def pilot(self, N: int) -> Pilot:
+        if N not in self._pilots:
+            pl = Pilot(self._pilot_bits(N), device=self.device)
+            check(lib().pnce_server_add_pilot(self._s, pl.handle), "pnce_server_add_pilot")
+            self._pilots[N] = pl
+        return self._pilots[N]
+
+    def prepare(self, Ns, caps=CAPACITIES[:3]):
+        """Capture the graphs of every (N, lag class) bucket of the given PN lengths, for
+        every slot and capacity, before serving starts."""
+        with torch.cuda.device(self.device):
+            for N in Ns:
+                self.pilot(N)
+                for klc in sorted({kl_class(k, N) for k in KL_CLASSES if k <= N} | {kl_class(N, N)}):
+                    for c in caps:
+                        check(lib().pnce_server_prepare(self._s, N, klc, c),
+                              "pnce_server_prepare")
+
+    def run(self, requests: list) -> dict:
+        for N in {r.N for r in requests}:
+            self.pilot(N)
+        reqs = _req_table(requests)
+        out = np.empty(len(requests), dtype=OUT_DTYPE)
+        nb = C.c_int(0)
+        with torch.cuda.device(self.device):
+            st = lib().pnce_server_run(self._s, reqs.ctypes.data, len(requests),
+                                            out.ctypes.data, C.byref(nb))
+        if st == _lib.PNCE_EINVAL:
+            check(st, "pnce_server_run")
+        stats = _native_stats(requests, out, nb.value)
+        check(st, "pnce_server_run")                   # a status latched on the device
+        return stats
+
+    def __del__(self):
+        s = getattr(self, "_s", None)
+        if s is not None and _lib._lib is not None:
+            _lib._lib.pnce_server_destroy(s)
+            self._s = None

@@ -1,0 +1,57 @@
+"""The native serving loop's scheduling (pnce_sched_simulate: the C++ scheduler on a virtual
+clock, no GPU) makes exactly the decisions of the Python Server with the fake engine of
+test_serving_cpu on the same clock: same admission, launch and completion times, same
+batches."""
+import numpy as np
+import pytest
+
+from paper_2206_05506_gb300 import PnceError
+from paper_2206_05506_gb300.serve import Request, Server, simulate
+from synth import serving as S
+from test_serving_cpu import Clock, FakeEngine
+
+
+def _trace(rate, dur, seed):
+    specs = S.poisson_trace(rate, dur, seed=seed)
+    return [Request(s.rid, s.t_arrival, s.M, s.N, s.K, s.L, 0, 0) for s in specs]
+
+
+@pytest.mark.parametrize("slots,cap,rows,base,seed", [
+    (3, 1e12, 4096, 200e-6, 1),          # plenty of memory
+    (1, 1e12, 4096, 2e-3, 2),            # one slow slot: batches grow
+    (4, 3_000_000, 4096, 1e-3, 3),       # tight memory: admission waits
+    (2, 1e12, 300, 400e-6, 4),           # small batches: packing limit
+])
+def test_simulation_matches_python_scheduler(slots, cap, rows, base, seed):
+    py = _trace(20000.0, 0.02, seed)
+    clock = Clock()
+    eng = FakeEngine(clock, slots=slots, base=base)
+    srv = Server(eng, mem_cap_bytes=cap, max_batch_rows=rows)
+    srv.run(py, clock=clock, t0=0.0)
+    out, nb = simulate(_trace(20000.0, 0.02, seed), slots, cap, rows, row_bytes=1000.0,
+                       base_s=base, per_row_s=0.2e-6, clock_dt=5e-6)
+    assert nb == srv.batches == len(eng.launched)
+    assert np.all(out["status"] == 0)
+    np.testing.assert_array_equal(out["t_admit"], [r.t_admit for r in py])
+    np.testing.assert_array_equal(out["t_launch"], [r.t_launch for r in py])
+    np.testing.assert_array_equal(out["t_done"], [r.t_done for r in py])
+    np.testing.assert_array_equal(out["batch"], [r.batch for r in py])
+    # each native batch holds the same requests as the Python one, in order
+    for b, (_, N, klc, rids, _) in enumerate(eng.launched):
+        assert list(np.flatnonzero(out["batch"] == b)) == rids
+
+
+def test_simulation_rejects_invalid_traces():
+    reqs = _trace(20000.0, 0.005, 5)
+    with pytest.raises(PnceError):
+        simulate(reqs, 0, 1e12)                       # no slot
+    bad = list(reqs)
+    bad[0], bad[1] = bad[1], bad[0]                   # arrivals out of order
+    with pytest.raises(PnceError):
+        simulate(bad, 2, 1e12)
+    r = reqs[0]
+    over = [Request(0, 0.0, r.M, r.N, r.N, 2, 0, 0)]  # K*L > N
+    with pytest.raises(PnceError):
+        simulate(over, 2, 1e12)
+    out, nb = simulate([], 2, 1e12)
+    assert nb == 0 and out.size == 0
