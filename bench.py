@@ -331,11 +331,11 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
     for dtype, name in (("fp16", "fp16_tensor_core"), ("fp32", "fp32_simt")):
         nat = serve.NativeServer(S.pilot_bits, device=dev, dtype=dtype, slots=4,
                                  mem_cap_bytes=40e9)
-        nat.prepare([255, 511, 1023, 2047])
+        nat.prepare([255, 511, 1023, 2047], caps=serve.CAPACITIES)
         st = measure(nat.run)
         del nat
         eng = serve.GpuEngine(S.pilot_bits, device=dev, dtype=dtype, slots=4)
-        eng.prepare([255, 511, 1023, 2047])
+        eng.prepare([255, 511, 1023, 2047], caps=serve.CAPACITIES)
         st["python_loop"] = measure(lambda rq: serve.Server(eng, mem_cap_bytes=40e9).run(rq))
         res[name] = st
         del eng

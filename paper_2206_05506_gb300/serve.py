@@ -27,6 +27,11 @@ taps) whose received blocks sit in page-locked host memory.  The loop
 Pilot tables and the per-shape buffers stay resident on the device.  Each request's result
 depends only on its own antenna rows (per-antenna scales, fixed reduction order), so it is
 the same alone and in any mix.
+
+NativeServer runs the same rules inside the library (pnce_server_run, C++): a Python loop
+spends tens of microseconds of host time per batch (descriptor table, graph replay, event),
+which bounds the batches per second it can start; the native loop spends a few.  Server
+stays for engines written in Python (and the fault-injection tests).
 """
 from __future__ import annotations
 
