@@ -334,7 +334,9 @@ pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
  * pnce_sched_simulate: the same scheduling rules on a virtual clock, no GPU: the clock
  *   advances by clock_dt at every pass of the loop, a batch of r antennas completes
  *   base_s + per_row_s * r seconds after its launch, a request's footprint is
- *   M * row_bytes.  Fills out[n] and *batches as pnce_server_run does.
+ *   M * row_bytes.  Faults made on the host: every fail_launch_every-th launch is refused
+ *   and every fail_done_every-th batch that started fails at completion (0: never); their
+ *   requests get PNCE_ECUDA.  Fills out[n] and *batches as pnce_server_run does.
  */
 typedef struct pnce_server pnce_server;
 typedef struct {
@@ -358,6 +360,7 @@ pnce_status pnce_server_run(pnce_server* server, const pnce_serve_req* reqs, int
 pnce_status pnce_sched_simulate(const pnce_serve_req* reqs, int n, int slots,
                                 double mem_cap_bytes, int max_batch_rows, double row_bytes,
                                 double base_s, double per_row_s, double clock_dt,
+                                int fail_launch_every, int fail_done_every,
                                 pnce_serve_out* out, int* batches);
 
 pnce_status pnce_gather_rows(const uint64_t* src_rows, int rows, int nelem, void* dst_dev,

@@ -87,7 +87,7 @@ _SIGS = {
     "pnce_server_prepare": (_i, [_vp, _i, _i, _i]),
     "pnce_server_run": (_i, [_vp, _vp, _i, _vp, C.POINTER(_i)]),
     "pnce_sched_simulate": (_i, [_vp, _i, _i, C.c_double, _i, C.c_double, C.c_double,
-                                 C.c_double, C.c_double, _vp, C.POINTER(_i)]),
+                                 C.c_double, C.c_double, _i, _i, _vp, C.POINTER(_i)]),
 }
 
 

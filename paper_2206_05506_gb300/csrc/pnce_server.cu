@@ -193,20 +193,34 @@ class Scheduler {
 };
 
 // Virtual time (no GPU): a batch of r rows takes base + per_row * r seconds; a request's
-// footprint is M * row_bytes; the clock advances by dt at every pass of the loop.
+// footprint is M * row_bytes; the clock advances by dt at every pass of the loop.  Faults
+// made on the host: every fail_launch-th launch is refused, and every fail_done-th batch
+// that started reports a failure when it completes (0: never).
 struct SimExec {
     double* t;
     double base, per_row, row_bytes;
+    int fail_launch, fail_done;
     std::vector<double> end;
-    std::vector<char> running;
+    std::vector<char> running, fault;
+    long long calls = 0, started = 0;
     double footprint(const pnce_serve_req& r) const { return (double)r.M * row_bytes; }
-    bool launch(int slot, int, int, const std::vector<int>&, long long rows, int*) {
+    bool launch(int slot, int, int, const std::vector<int>&, long long rows, int* status) {
+        ++calls;
+        if (fail_launch > 0 && calls % fail_launch == 0) {
+            *status = PNCE_ECUDA;
+            return false;
+        }
+        ++started;
         end[(size_t)slot] = *t + base + per_row * (double)rows;
         running[(size_t)slot] = 1;
+        fault[(size_t)slot] = fail_done > 0 && started % fail_done == 0;
         return true;
     }
     int done(int slot) {
-        if (running[(size_t)slot] && *t >= end[(size_t)slot]) running[(size_t)slot] = 0;
+        if (running[(size_t)slot] && *t >= end[(size_t)slot]) {
+            running[(size_t)slot] = 0;
+            if (fault[(size_t)slot]) return -1;
+        }
         return running[(size_t)slot] ? 0 : 1;
     }
 };
@@ -230,12 +244,15 @@ bool serve_args_ok(const pnce_serve_req* reqs, int n, const pnce_serve_out* out,
 extern "C" pnce_status pnce_sched_simulate(const pnce_serve_req* reqs, int n, int slots,
                                            double mem_cap, int max_batch_rows, double row_bytes,
                                            double base_s, double per_row_s, double clock_dt,
+                                           int fail_launch_every, int fail_done_every,
                                            pnce_serve_out* out, int* batches) {
     if (!serve_args_ok(reqs, n, out, slots, mem_cap, max_batch_rows) || !(clock_dt > 0.0) ||
-        !(base_s >= 0.0) || !(per_row_s >= 0.0) || !(row_bytes >= 0.0))
+        !(base_s >= 0.0) || !(per_row_s >= 0.0) || !(row_bytes >= 0.0) ||
+        fail_launch_every < 0 || fail_done_every < 0)
         return PNCE_EINVAL;
     double t = 0.0;
-    SimExec ex{&t, base_s, per_row_s, row_bytes, std::vector<double>((size_t)slots, 0.0),
+    SimExec ex{&t, base_s, per_row_s, row_bytes, fail_launch_every, fail_done_every,
+               std::vector<double>((size_t)slots, 0.0), std::vector<char>((size_t)slots, 0),
                std::vector<char>((size_t)slots, 0)};
     Scheduler<SimExec> sch(ex, reqs, n, out, slots, mem_cap, max_batch_rows);
     while (!sch.finished()) {

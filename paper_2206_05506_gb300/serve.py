@@ -391,15 +391,18 @@ def _native_stats(requests: list, out: np.ndarray, batches: int) -> dict:
 
 def simulate(requests: list, slots: int, mem_cap_bytes: float, max_batch_rows: int = 4096,
              row_bytes: float = 1000.0, base_s: float = 200e-6, per_row_s: float = 0.2e-6,
-             clock_dt: float = 5e-6):
+             clock_dt: float = 5e-6, fail_launch_every: int = 0, fail_done_every: int = 0):
     """The native loop's scheduling on a virtual clock, no GPU (pnce_sched_simulate):
-    returns (per-request results as OUT_DTYPE, number of batches)."""
+    returns (per-request results as OUT_DTYPE, number of batches).  fail_*_every: faults
+    made on the host (every n-th launch refused, every n-th started batch failing when it
+    completes)."""
     reqs = _req_table(requests)
     out = np.empty(len(requests), dtype=OUT_DTYPE)
     nb = C.c_int(0)
     check(lib().pnce_sched_simulate(reqs.ctypes.data, len(requests), slots,
                                          float(mem_cap_bytes), max_batch_rows, float(row_bytes),
                                          float(base_s), float(per_row_s), float(clock_dt),
+                                         int(fail_launch_every), int(fail_done_every),
                                          out.ctypes.data, C.byref(nb)), "pnce_sched_simulate")
     return out, nb.value
 

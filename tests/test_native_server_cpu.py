@@ -55,3 +55,23 @@ def test_simulation_rejects_invalid_traces():
         simulate(over, 2, 1e12)
     out, nb = simulate([], 2, 1e12)
     assert nb == 0 and out.size == 0
+
+
+def test_simulated_faults_match_python_loop():
+    # batches whose launch is refused or that fail at completion (faults made on the host):
+    # the same requests fail, at the same times, and every slot and byte comes back
+    from test_serving_cpu import FlakyEngine
+    py = _trace(20000.0, 0.03, 5)
+    clock = Clock()
+    eng = FlakyEngine(clock, slots=3)
+    srv = Server(eng, mem_cap_bytes=2e6, max_batch_rows=1024)
+    srv.run(py, clock=clock, t0=0.0)
+    out, nb = simulate(_trace(20000.0, 0.03, 5), 3, 2e6, 1024, fail_launch_every=5,
+                       fail_done_every=7)
+    failed = {r.rid for r in srv.failed}
+    assert failed and len(failed) < len(py)
+    assert set(np.flatnonzero(out["status"] != 0)) == failed
+    assert np.all(out["status"][list(failed)] == 4)          # PNCE_ECUDA
+    np.testing.assert_array_equal(out["t_done"], [r.t_done for r in py])
+    np.testing.assert_array_equal(out["t_launch"], [r.t_launch for r in py])
+    assert nb == srv.batches
