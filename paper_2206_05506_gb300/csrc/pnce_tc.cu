@@ -1607,7 +1607,19 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     // lag tile width: as few tiles of <= 256 lags as cover a run, split evenly (a run is
     // all K*L lags when they are contiguous, one transmitter's L lags otherwise)
     const int run = lags.mode == 0 ? lags.ldH : lags.L;
-    const int tiles_per_run = (run + MAX_BN - 1) / MAX_BN;
+    // A launch of few tiles (a serving batch) leaves most SMs idle, and a CTA's epilogue
+    // drains its 128 x 256 accumulator at the rate one SM's stores reach (~4 us per tile):
+    // there, tiles of <= 128 lags give twice the CTAs and half the drain each, for MMAs of
+    // N = 128 (which the shared-memory data path makes ~1.5x dearer per flop).
+    // PNCE_TC_SMALL_GRID_BN=0 keeps 256 (to compare the two).
+    int max_bn = MAX_BN;
+    if (lags.mode == 0) {
+        const long long rb = (pnce::operand_rows(A) + BM - 1) / BM;
+        const long long t256 = rb * ((run + MAX_BN - 1) / MAX_BN);
+        const char* sg = getenv("PNCE_TC_SMALL_GRID_BN");
+        if (2 * t256 <= h->num_sms && !(sg && sg[0] == '0')) max_bn = 128;
+    }
+    const int tiles_per_run = (run + max_bn - 1) / max_bn;
     const int per = (run + tiles_per_run - 1) / tiles_per_run;
     prm.BN = (per + 31) / 32 * 32;
     // Lag tiles of at most 128 lags each (a transmitter's lags under the spread shift rule)
