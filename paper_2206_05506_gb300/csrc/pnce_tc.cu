@@ -39,6 +39,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <mutex>
 
 #include "pnce_internal.h"
@@ -1611,13 +1612,16 @@ pnce_status launch_dt(const pnce_handle* h, const pnce_pilot* pilot, long long A
     // drains its 128 x 256 accumulator at the rate one SM's stores reach (~4 us per tile):
     // there, tiles of <= 128 lags give twice the CTAs and half the drain each, for MMAs of
     // N = 128 (which the shared-memory data path makes ~1.5x dearer per flop).
-    // PNCE_TC_SMALL_GRID_BN=0 keeps 256 (to compare the two).
+    // The width halves while the tiles still fill at most half the SMs, down to
+    // PNCE_TC_SMALL_GRID_BN (default 128; 0 keeps 256, to compare).
     int max_bn = MAX_BN;
     if (lags.mode == 0) {
         const long long rb = (pnce::operand_rows(A) + BM - 1) / BM;
-        const long long t256 = rb * ((run + MAX_BN - 1) / MAX_BN);
         const char* sg = getenv("PNCE_TC_SMALL_GRID_BN");
-        if (2 * t256 <= h->num_sms && !(sg && sg[0] == '0')) max_bn = 128;
+        const int floor_bn = sg ? atoi(sg) : 128;
+        while (floor_bn > 0 && max_bn / 2 >= floor_bn &&
+               2 * rb * ((run + max_bn - 1) / max_bn) <= h->num_sms)
+            max_bn /= 2;
     }
     const int tiles_per_run = (run + max_bn - 1) / max_bn;
     const int per = (run + tiles_per_run - 1) / tiles_per_run;
