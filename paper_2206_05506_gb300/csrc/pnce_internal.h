@@ -153,6 +153,18 @@ QuantLayout quant_layout(long long A, int N, int dtype);
 cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long A, int N,
                              int KL, float2* H, cudaStream_t s);
 // general form: rows of Y y_stride elements apart (first sample at Y), lags per `lags`
+// Serving batches on the FP32 path: batch row a is row a - row_offset of request
+// dd[row_req[a]] (row_req < 0: no request); each row's first K*L lags are written into its
+// request's H, and the rows are read from the requests' Y when Yb is null, else from Yb (a
+// batch copy at pitch N).  simt_grouped_ok: where the warp kernel applies (kl_max > 32 and
+// a pilot window within its shared-memory copy; cudaErrorNotSupported otherwise);
+// simt_grouped_reads_rows: where reading from the requests pays (one lag tile covers
+// kl_max).  pdl: launch as a programmatic dependent of the kernel before it.
+bool simt_grouped_ok(int N, int kl_max);
+bool simt_grouped_reads_rows(int kl_max);
+cudaError_t launch_simt_grouped(const pnce_pilot* pilot, const pnce_req_desc* dd,
+                                const int* row_req, long long rows, int N, int kl_max,
+                                const float2* Yb, cudaStream_t s, bool pdl);
 cudaError_t launch_simt_bits_ex(const pnce_pilot* pilot, const float2* Y, long long y_stride,
                                 long long A, int N, const LagMap& lags, float2* H,
                                 cudaStream_t s);

@@ -236,12 +236,28 @@ pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
     int* row_req = reinterpret_cast<int*>(ws + lay.m_off);
     // prep (table copy + row map), then every kernel as a programmatic dependent of the one
     // before it: four graph nodes on the tensor-core path (prep, gather-quantise,
-    // correlation, scatter)
+    // correlation, scatter), two or three on the FP32 path (prep, a row gather when the lags
+    // span several tiles, the correlation writing into the requests' results)
     grouped_prep_kernel<<<1, PREP_THREADS, 0, s>>>(descs, nreq, rows, kl_max, dd, row_req,
                                                    h->status_dev);
     if (cudaGetLastError() != cudaSuccess) return PNCE_ECUDA;
     if (dtype == PNCE_FP32_SIMT) {
         float2* Yb = reinterpret_cast<float2*>(ws + lay.y_off);
+        if (pnce::simt_grouped_ok(N, kl_max)) {
+            // the SIMT kernel writes each row's lags into its request; it reads the rows
+            // from the requests too when one lag tile covers kl_max, else from a row gather
+            const bool direct = pnce::simt_grouped_reads_rows(kl_max);
+            if (!direct && launch_dependent(grouped_gather_kernel, (unsigned)rows, THREADS, s,
+                                            (const pnce_req_desc*)dd, (const int*)row_req, N,
+                                            Yb) != cudaSuccess)
+                return PNCE_ECUDA;
+            pnce::TraceScope tr(h, s, pnce::TRACE_SIMT);
+            return pnce::launch_simt_grouped(pilot, dd, row_req, rows, N, kl_max,
+                                             direct ? nullptr : Yb, s, !h->trace_on) ==
+                           cudaSuccess
+                       ? PNCE_OK
+                       : PNCE_ECUDA;
+        }
         if (launch_dependent(grouped_gather_kernel, (unsigned)rows, THREADS, s,
                              (const pnce_req_desc*)dd, (const int*)row_req, N, Yb) != cudaSuccess)
             return PNCE_ECUDA;

@@ -201,23 +201,52 @@ __host__ __device__ constexpr size_t win_bytes(int nred) {
     return ((size_t)win_len(nred) + (size_t)win_len(nred) / 32 + 1) * sizeof(float);
 }
 
-// The rows of one warp: NR (<= RA) received rows from row r0 of the group, the chunks of
-// the reduction double-buffered in the warp's own shared buffers.  Every output is summed
-// over n in the same order whatever NR, so results do not depend on the row split.
-template <int MODE, int RA, int NR>
+// Serving batches: row a of the launch is row a - row_offset of request dd[row_req[a]]
+// (its Y has N samples per row, its H keeps the first K*L lags); rows with row_req < 0
+// belong to no request.  The kernel writes each row's lags into its request's H, and reads
+// the rows from the requests' Y when Y is null (else from Y, a batch copy at pitch N):
+// no batch copy of H, and none of Y when one lag tile covers the lags (each row is then
+// read by one block; with more, every block of a row would fetch it over the host link).
+// Launched as a programmatic dependent of the kernel before it.  dd == nullptr: plain
+// Y / H.
+struct GroupedIO {
+    const pnce_req_desc* dd = nullptr;
+    const int* row_req = nullptr;
+    bool pdl = false;
+};
+
+// The rows of one warp: NR (<= RA) received rows from row a_first of the group, the chunks
+// of the reduction double-buffered in the warp's own shared buffers.  Every output is
+// summed over n in the same order whatever NR, so results do not depend on the row split.
+template <int MODE, int RA, int NR, bool GRP>
 __device__ __forceinline__ void warp_rows(WSmem<RA>& sm, const float* __restrict__ E,
                                           const float2* __restrict__ Y, long long y_stride,
                                           long long a_first, int N, const pnce::LagMap& lags,
                                           int col0, int valid, float invN,
-                                          float2* __restrict__ H, int warp, int lane) {
+                                          float2* __restrict__ H, int warp, int lane,
+                                          const GroupedIO& g) {
     const int nchunks = (N + NC - 1) / NC;
+    // row i's samples (null: no request owns it), looked up when needed rather than kept
+    // in registers through the main loop
+    auto src_row = [&](int i) -> const float2* {
+        const long long a = a_first + i;
+        if (!GRP || Y != nullptr) return Y + a * y_stride;
+        const int b = __ldg(g.row_req + a);
+        if (b < 0) return nullptr;
+        const pnce_req_desc& q = g.dd[b];
+        return static_cast<const float2*>(q.Y) + (a - q.row_offset) * N;
+    };
+    // a valid address for the copies that only zero-fill
+    const float2* zsrc = (!GRP || Y) ? Y : reinterpret_cast<const float2*>(g.row_req);
     auto stage = [&](int c, int buf) {
         const int n0 = c * NC;
-        for (int i = lane; i < NR * NC; i += 32) {
-            const int aa = i / NC, nn = i % NC;
-            const bool ok = n0 + nn < N;
-            const float2* src = ok ? (Y + (a_first + aa) * y_stride + n0 + nn) : Y;
-            cp_async8(&sm.y[warp][buf][aa][nn], src, ok);
+#pragma unroll
+        for (int aa = 0; aa < NR; ++aa) {
+            const float2* sr = src_row(aa);
+            for (int nn = lane; nn < NC; nn += 32) {
+                const bool ok = sr != nullptr && n0 + nn < N;
+                cp_async8(&sm.y[warp][buf][aa][nn], ok ? sr + n0 + nn : zsrc, ok);
+            }
         }
         asm volatile("cp.async.commit_group;\n" ::: "memory");
     };
@@ -278,23 +307,54 @@ __device__ __forceinline__ void warp_rows(WSmem<RA>& sm, const float* __restrict
         __syncwarp();                          // buf is free for chunk c + 2
     }
 
+    if constexpr (!GRP) {
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            float2* hrow = H + (a_first + i) * lags.ldH + col0;
+#pragma unroll
+            for (int r = 0; r < RJ; ++r) {
+                const int j = RJ * lane + r;
+                if (j < valid) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
+            }
+        }
+        return;
+    } else {
+    // Serving rows go out through the warp's (now idle) staging buffer, so that a store
+    // instruction writes 256 contiguous bytes rather than 32 pieces of 8 bytes 64 bytes
+    // apart: the same for L2, but over the host link (results in page-locked memory) every
+    // partial piece would be a transfer of its own.
+    float2* sbuf = &sm.y[warp][0][0][0];             // 2 * RA * NC >= TJ entries
+    static_assert(2 * RA * NC >= TJ, "staging buffer too small for a row of results");
 #pragma unroll
     for (int i = 0; i < NR; ++i) {
-        float2* hrow = H + (a_first + i) * lags.ldH + col0;
+        const long long a = a_first + i;
+        const int b = __ldg(g.row_req + a);
+        if (b < 0) continue;                         // warp-uniform: one row per iteration
+        const pnce_req_desc& q = g.dd[b];
+        const int kl = q.K * q.L;
+        float2* drow = static_cast<float2*>(q.H) + (a - q.row_offset) * kl + col0;
+        const int vrow = min(valid, kl - col0);      // lags of the tile kept for it
 #pragma unroll
-        for (int r = 0; r < RJ; ++r) {
-            const int j = RJ * lane + r;
-            if (j < valid) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
+        for (int r = 0; r < RJ; ++r)
+            sbuf[RJ * lane + r] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < RJ; ++k) {
+            const int j = lane + 32 * k;
+            if (j < vrow) drow[j] = sbuf[j];
         }
+        __syncwarp();                                // sbuf is rewritten for the next row
+    }
     }
 }
 
-template <int MODE, int RA>
+template <int MODE, int RA, bool GRP>
 __global__ void __launch_bounds__(256, 2)
 simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict__ preal,
                       const float2* __restrict__ Y, long long y_stride, long long A,
                       int N /* reduction length */, const pnce::LagMap lags, int nmod,
-                      int num_jt, long long groups, float invN, float2* __restrict__ H) {
+                      int num_jt, long long groups, float invN, float2* __restrict__ H,
+                      const GroupedIO gio) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     WSmem<RA>& sm = *reinterpret_cast<WSmem<RA>*>(smem_raw);
     float* E = reinterpret_cast<float*>(smem_raw + sizeof(WSmem<RA>));
@@ -322,6 +382,9 @@ simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict
         }
     }
     __syncthreads();
+    // as a programmatic dependent (serving batches) the pilot window above overlapped the
+    // kernel before; the row map and the rows are read only after it has finished
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     // The group's rows spread over the warps as evenly as possible (rows / WARPS or one
     // more each), so that the four SM sub-partitions, which take warps w, w + 4 of each
     // block, carry nearly the same number of rows (27 rows as 4+4+4+3+3+3+3+3 rather than
@@ -331,19 +394,19 @@ simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict
     const long long a_first = a0 + (long long)warp * rbase + (warp < rextra ? warp : rextra);
     if (nrw == 4) {
         if constexpr (RA >= 4)
-            warp_rows<MODE, RA, 4>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
-                                   warp, lane);
+            warp_rows<MODE, RA, 4, GRP>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
+                                   warp, lane, gio);
     } else if (nrw == 3) {
         if constexpr (RA >= 3)
-            warp_rows<MODE, RA, 3>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
-                                   warp, lane);
+            warp_rows<MODE, RA, 3, GRP>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
+                                   warp, lane, gio);
     } else if (nrw == 2) {
         if constexpr (RA >= 2)
-            warp_rows<MODE, RA, 2>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
-                                   warp, lane);
+            warp_rows<MODE, RA, 2, GRP>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
+                                   warp, lane, gio);
     } else if (nrw == 1) {
-        warp_rows<MODE, RA, 1>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H, warp,
-                               lane);
+        warp_rows<MODE, RA, 1, GRP>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H, warp,
+                               lane, gio);
     }
 }
 
@@ -477,20 +540,41 @@ constexpr int FEW_LAGS = 32;    // largest K*L the few-lags kernel takes
 template <int MODE, int RA>
 cudaError_t launch_ra(const uint32_t* bits, const float* preal, const float2* Y,
                       long long y_stride, long long A, int N, const pnce::LagMap& lags, int nmod,
-                      int num_jt, long long groups, float2* H, cudaStream_t s) {
+                      int num_jt, long long groups, float2* H, cudaStream_t s,
+                      const GroupedIO& g) {
     const long long blocks = (long long)num_jt * groups;
     if (blocks > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     if (win_len(N) <= WIN_MAX) {
         const size_t wsmem = sizeof(WSmem<RA>) + win_bytes(N);
-        cudaError_t e = cudaFuncSetAttribute(simt_corr_warp_kernel<MODE, RA>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+        auto kern = simt_corr_warp_kernel<MODE, RA, false>;
+        if constexpr (MODE == FWD_BITS) {
+            if (g.dd) kern = simt_corr_warp_kernel<MODE, RA, true>;
+        } else {
+            if (g.dd) return cudaErrorNotSupported;
+        }
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)wsmem);
         if (e != cudaSuccess) return e;
-        simt_corr_warp_kernel<MODE, RA><<<(unsigned)blocks, 256, wsmem, s>>>(
-            bits, preal, Y, y_stride, A, N, lags, nmod, num_jt, groups,
-            (float)(1.0 / (double)nmod), H);
+        const float invN = (float)(1.0 / (double)nmod);
+        if (g.pdl) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3((unsigned)blocks, 1, 1);
+            cfg.blockDim = dim3(256, 1, 1);
+            cfg.dynamicSmemBytes = wsmem;
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+            at[0].val.programmaticStreamSerializationAllowed = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            return cudaLaunchKernelEx(&cfg, kern, bits, preal, Y, y_stride, A, N, lags, nmod,
+                                      num_jt, groups, invN, H, g);
+        }
+        kern<<<(unsigned)blocks, 256, wsmem, s>>>(bits, preal, Y, y_stride, A, N, lags, nmod,
+                                                  num_jt, groups, invN, H, g);
         return cudaGetLastError();
     }
+    if (g.dd) return cudaErrorNotSupported;    // the row I/O exists in the warp kernel only
     const size_t smem = sizeof(Smem<RA>);
     cudaError_t e = cudaFuncSetAttribute(simt_corr_kernel<MODE, RA>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -505,7 +589,7 @@ cudaError_t launch_ra(const uint32_t* bits, const float* preal, const float2* Y,
 template <int MODE>
 cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, long long y_stride,
                    long long A, int N, const pnce::LagMap& lags, int nmod, float2* H,
-                   cudaStream_t s) {
+                   cudaStream_t s, const GroupedIO& g = GroupedIO{}) {
     const long long num_jt_ll = pnce::lag_tiles(lags, TJ);
     if (num_jt_ll > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     const int num_jt = (int)num_jt_ll;
@@ -528,7 +612,7 @@ cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, lo
         // A small grid (less than half of the resident 32-row blocks): blocks of 8 rows, one
         // antenna per thread, so each block is 4x shorter and a small batch finishes sooner.
         return launch_ra<MODE, 1>(bits, preal, Y, y_stride, A, N, lags, nmod, num_jt,
-                                  (A + WARPS - 1) / WARPS, H, s);
+                                  (A + WARPS - 1) / WARPS, H, s, g);
     }
     // Otherwise 32-row groups, raised so that the grid fills whole waves of the resident
     // blocks (tiles of 2^k rows leave the last wave partly empty on 152 SMs).  Neither choice
@@ -538,7 +622,8 @@ cudaError_t launch(const uint32_t* bits, const float* preal, const float2* Y, lo
         const long long even = waves * slots / num_jt;
         groups = std::min(A, std::max(groups, even));
     }
-    return launch_ra<MODE, 4>(bits, preal, Y, y_stride, A, N, lags, nmod, num_jt, groups, H, s);
+    return launch_ra<MODE, 4>(bits, preal, Y, y_stride, A, N, lags, nmod, num_jt, groups, H, s,
+                              g);
 }
 
 }  // namespace
@@ -550,6 +635,21 @@ cudaError_t launch_simt_bits(const pnce_pilot* pilot, const float2* Y, long long
     if (KL <= FEW_LAGS) return launch_few_lags(pilot->ext_bits_dev, Y, N, A, N, KL, KL, H, s);
     return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Y, N, A, N, lagmap_contiguous(KL), N,
                             H, s);
+}
+
+bool simt_grouped_ok(int N, int kl_max) { return kl_max > FEW_LAGS && win_len(N) <= WIN_MAX; }
+bool simt_grouped_reads_rows(int kl_max) { return kl_max <= TJ; }
+
+cudaError_t launch_simt_grouped(const pnce_pilot* pilot, const pnce_req_desc* dd,
+                                const int* row_req, long long rows, int N, int kl_max,
+                                const float2* Yb, cudaStream_t s, bool pdl) {
+    if (!simt_grouped_ok(N, kl_max)) return cudaErrorNotSupported;
+    GroupedIO g;
+    g.dd = dd;
+    g.row_req = row_req;
+    g.pdl = pdl;
+    return launch<FWD_BITS>(pilot->ext_bits_dev, nullptr, Yb, N, rows, N,
+                            lagmap_contiguous(kl_max), N, nullptr, s, g);
 }
 
 cudaError_t launch_simt_bits_ex(const pnce_pilot* pilot, const float2* Y, long long y_stride,
