@@ -280,11 +280,16 @@ pnce_status pnce_trace_read(pnce_handle* h, int* kinds, float* ms, int max_entri
  * memory (read and written by the GPU over the host link), 8-byte aligned.  M = 0 marks
  * an empty slot.  A descriptor with row_offset + M > rows, K*L > kl_max, or a NULL or
  * misaligned buffer is skipped and latches PNCE_EINVAL (pnce_get_status), as does a row
- * claimed by two descriptors (which of the two then gets it is not defined).  Batch rows no request covers are estimated from
- * whatever the workspace holds and discarded.  workspace_dev: 256-byte aligned,
- * pnce_grouped_workspace_size(rows, N, kl_max, dtype) bytes (0 for invalid shapes).
- * Enqueues gather, quantiser (tensor-core dtypes), correlation and scatter kernels on
- * `stream`; allocates nothing.
+ * claimed by two descriptors (which of the two then gets it is not defined).  Batch rows
+ * no request covers are estimated from zeros or whatever the workspace holds, and
+ * discarded.  workspace_dev: 256-byte aligned, pnce_grouped_workspace_size(rows, N,
+ * kl_max, dtype) bytes (0 for invalid shapes).  Enqueues on `stream`, each kernel a
+ * programmatic dependent of the one before it: a table / row-map kernel, then for the
+ * tensor-core dtypes the quantiser (reading each row from its request's Y), the
+ * correlation and a scatter into the requests' H; for FP32 with kl_max > 32 the SIMT
+ * correlation reading the rows from the requests' Y (after a row gather into the
+ * workspace when kl_max > 256) and writing each row's lags into its request's H; for
+ * FP32 with kl_max <= 32 a row gather, the correlation and a scatter.  Allocates nothing.
  */
 typedef struct {
     const void* Y;          /* complex64 [M][N] */
@@ -319,7 +324,9 @@ pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
  * pnce_server_create: dtype as pnce_estimate_grouped (PNCE_AUTO resolved per bucket);
  *   1 <= slots <= 64.  Creates the streams and events; the caller keeps h alive.
  * pnce_server_add_pilot: the pilot for one PN length N (not owned: keep it alive while
- *   the server runs).  A request whose N has no pilot fails (status PNCE_EINVAL).
+ *   the server may run batches of that N).  A request whose N has no pilot fails (status
+ *   PNCE_EINVAL).  Adding another pilot for an N drops the graphs captured with the
+ *   previous one (after the server's streams are idle), so that one may then be destroyed.
  * pnce_server_prepare: captures the graphs of one (N, kl_class, capacity) shape on every
  *   slot ahead of a run (a run captures missing shapes when it first needs them, inside
  *   its timed loop).  Allocates the shape's workspace and page-locked descriptor table.

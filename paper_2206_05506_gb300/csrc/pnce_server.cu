@@ -476,6 +476,21 @@ pnce_status pnce_server_destroy(pnce_server* sv) {
 pnce_status pnce_server_add_pilot(pnce_server* sv, const pnce_pilot* pilot) {
     if (!sv || !pilot) return PNCE_EINVAL;
     if (pilot->device != sv->h->device) return PNCE_ESTATE;
+    auto it = sv->pilots.find(pilot->N);
+    if (it != sv->pilots.end() && it->second != pilot) {
+        // the graphs captured for this N read the old pilot's table: drop them (they are
+        // captured again on first use), so the old pilot may be destroyed
+        for (cudaStream_t s : sv->streams)
+            if (cudaStreamSynchronize(s) != cudaSuccess) return PNCE_ECUDA;
+        for (auto sit = sv->shapes.begin(); sit != sv->shapes.end();) {
+            if (std::get<1>(sit->first) == pilot->N) {
+                free_shape(sit->second.get());
+                sit = sv->shapes.erase(sit);
+            } else {
+                ++sit;
+            }
+        }
+    }
     sv->pilots[pilot->N] = pilot;
     return PNCE_OK;
 }

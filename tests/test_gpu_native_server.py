@@ -111,3 +111,29 @@ def test_native_memory_cap(setup):
     st = nat.run(reqs)
     assert st["requests"] == len(reqs) and st["failed"] == 0
     assert any(r.t_admit > r.t_arrival for r in reqs)
+
+
+def test_native_pilot_replacement_recaptures(setup):
+    # a new pilot for an N drops the graphs captured with the old one, which may then go
+    import gc
+    from paper_2206_05506_gb300 import Pilot, lib
+    serve, pool, pinned = setup
+    dev = torch.device("cuda", 0)
+    specs = [s for s in S.poisson_trace(20000.0, 0.01, seed=24, payload_slots=2)
+             if s.N == 1023][:20]
+    total = sum(s.M * s.K * s.L for s in specs)
+    out = torch.zeros(total, dtype=torch.complex64, pin_memory=True)
+    nat = serve.NativeServer(S.pilot_bits, device=dev, dtype="fp16", slots=2)
+    nat.prepare([1023], caps=(64, 256))
+    new = Pilot(S.pilot_bits(1023), device=dev)
+    assert lib().pnce_server_add_pilot(nat._s, new.handle) == 0
+    old, nat._pilots[1023] = nat._pilots[1023], new
+    del old
+    gc.collect()                                     # the old pilot's table is freed
+    reqs = _requests(serve, pinned, specs, out)
+    st = nat.run(reqs)
+    assert st["requests"] == len(reqs) and st["failed"] == 0
+    for r in reqs:
+        ref = O.estimate(pool[(r.M, r.N)][[specs[reqs.index(r)].slot]], S.pilot_bits(r.N),
+                         r.K, r.L)
+        assert O.nmse(_result(out, r)[None], ref) <= TOL["fp16"]
