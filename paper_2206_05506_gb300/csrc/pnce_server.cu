@@ -239,6 +239,17 @@ bool serve_args_ok(const pnce_serve_req* reqs, int n, const pnce_serve_out* out,
     return true;
 }
 
+// The entry points allocate through the standard library; nothing may throw across the C
+// boundary, so an exception (out of host memory) becomes PNCE_ENOMEM.
+template <class F>
+pnce_status guarded(F&& f) {
+    try {
+        return f();
+    } catch (...) {
+        return PNCE_ENOMEM;
+    }
+}
+
 }  // namespace
 
 extern "C" pnce_status pnce_sched_simulate(const pnce_serve_req* reqs, int n, int slots,
@@ -250,17 +261,19 @@ extern "C" pnce_status pnce_sched_simulate(const pnce_serve_req* reqs, int n, in
         !(base_s >= 0.0) || !(per_row_s >= 0.0) || !(row_bytes >= 0.0) ||
         fail_launch_every < 0 || fail_done_every < 0)
         return PNCE_EINVAL;
-    double t = 0.0;
-    SimExec ex{&t, base_s, per_row_s, row_bytes, fail_launch_every, fail_done_every,
-               std::vector<double>((size_t)slots, 0.0), std::vector<char>((size_t)slots, 0),
-               std::vector<char>((size_t)slots, 0)};
-    Scheduler<SimExec> sch(ex, reqs, n, out, slots, mem_cap, max_batch_rows);
-    while (!sch.finished()) {
-        t += clock_dt;
-        sch.step(t);
-    }
-    if (batches) *batches = sch.batches();
-    return PNCE_OK;
+    return guarded([&] {
+        double t = 0.0;
+        SimExec ex{&t, base_s, per_row_s, row_bytes, fail_launch_every, fail_done_every,
+                   std::vector<double>((size_t)slots, 0.0), std::vector<char>((size_t)slots, 0),
+                   std::vector<char>((size_t)slots, 0)};
+        Scheduler<SimExec> sch(ex, reqs, n, out, slots, mem_cap, max_batch_rows);
+        while (!sch.finished()) {
+            t += clock_dt;
+            sch.step(t);
+        }
+        if (batches) *batches = sch.batches();
+        return PNCE_OK;
+    });
 }
 
 namespace {
@@ -439,28 +452,30 @@ pnce_status pnce_server_create(pnce_handle* h, int dtype, int slots, double mem_
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return PNCE_ECUDA;
     if (dev != h->device) return PNCE_ESTATE;
-    auto sv = std::make_unique<pnce_server>();
-    sv->h = h;
-    sv->dtype = dtype;
-    sv->slots = slots;
-    sv->mem_cap = mem_cap_bytes;
-    sv->max_rows = max_batch_rows;
-    for (int i = 0; i < slots; ++i) {
-        cudaStream_t s = nullptr;
-        cudaEvent_t e = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            pnce_server_destroy(sv.release());
-            return PNCE_ECUDA;
+    return guarded([&]() -> pnce_status {
+        auto sv = std::make_unique<pnce_server>();
+        sv->h = h;
+        sv->dtype = dtype;
+        sv->slots = slots;
+        sv->mem_cap = mem_cap_bytes;
+        sv->max_rows = max_batch_rows;
+        for (int i = 0; i < slots; ++i) {
+            cudaStream_t s = nullptr;
+            cudaEvent_t e = nullptr;
+            if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+                pnce_server_destroy(sv.release());
+                return PNCE_ECUDA;
+            }
+            sv->streams.push_back(s);
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+                pnce_server_destroy(sv.release());
+                return PNCE_ECUDA;
+            }
+            sv->events.push_back(e);
         }
-        sv->streams.push_back(s);
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            pnce_server_destroy(sv.release());
-            return PNCE_ECUDA;
-        }
-        sv->events.push_back(e);
-    }
-    *out = sv.release();
-    return PNCE_OK;
+        *out = sv.release();
+        return PNCE_OK;
+    });
 }
 
 pnce_status pnce_server_destroy(pnce_server* sv) {
@@ -476,33 +491,37 @@ pnce_status pnce_server_destroy(pnce_server* sv) {
 pnce_status pnce_server_add_pilot(pnce_server* sv, const pnce_pilot* pilot) {
     if (!sv || !pilot) return PNCE_EINVAL;
     if (pilot->device != sv->h->device) return PNCE_ESTATE;
-    auto it = sv->pilots.find(pilot->N);
-    if (it != sv->pilots.end() && it->second != pilot) {
-        // the graphs captured for this N read the old pilot's table: drop them (they are
-        // captured again on first use), so the old pilot may be destroyed
-        for (cudaStream_t s : sv->streams)
-            if (cudaStreamSynchronize(s) != cudaSuccess) return PNCE_ECUDA;
-        for (auto sit = sv->shapes.begin(); sit != sv->shapes.end();) {
-            if (std::get<1>(sit->first) == pilot->N) {
-                free_shape(sit->second.get());
-                sit = sv->shapes.erase(sit);
-            } else {
-                ++sit;
+    return guarded([&]() -> pnce_status {
+        auto it = sv->pilots.find(pilot->N);
+        if (it != sv->pilots.end() && it->second != pilot) {
+            // the graphs captured for this N read the old pilot's table: drop them (they are
+            // captured again on first use), so the old pilot may be destroyed
+            for (cudaStream_t s : sv->streams)
+                if (cudaStreamSynchronize(s) != cudaSuccess) return PNCE_ECUDA;
+            for (auto sit = sv->shapes.begin(); sit != sv->shapes.end();) {
+                if (std::get<1>(sit->first) == pilot->N) {
+                    free_shape(sit->second.get());
+                    sit = sv->shapes.erase(sit);
+                } else {
+                    ++sit;
+                }
             }
         }
-    }
-    sv->pilots[pilot->N] = pilot;
-    return PNCE_OK;
+        sv->pilots[pilot->N] = pilot;
+        return PNCE_OK;
+    });
 }
 
 pnce_status pnce_server_prepare(pnce_server* sv, int N, int kl_class_, int capacity) {
     if (!sv || capacity < 1 || kl_class_ < 1 || kl_class_ > N) return PNCE_EINVAL;
-    for (int slot = 0; slot < sv->slots; ++slot) {
-        ServeShape* sh = nullptr;
-        const pnce_status st = get_shape(sv, slot, N, kl_class_, capacity, &sh);
-        if (st != PNCE_OK) return st;
-    }
-    return PNCE_OK;
+    return guarded([&] {
+        for (int slot = 0; slot < sv->slots; ++slot) {
+            ServeShape* sh = nullptr;
+            const pnce_status st = get_shape(sv, slot, N, kl_class_, capacity, &sh);
+            if (st != PNCE_OK) return st;
+        }
+        return PNCE_OK;
+    });
 }
 
 pnce_status pnce_server_run(pnce_server* sv, const pnce_serve_req* reqs, int n,
@@ -514,13 +533,22 @@ pnce_status pnce_server_run(pnce_server* sv, const pnce_serve_req* reqs, int n,
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return PNCE_ECUDA;
     if (dev != sv->h->device) return PNCE_ESTATE;
-    CudaExecBound ex{CudaExec{sv, operand_elt(sv->dtype)}, reqs};
-    Scheduler<CudaExecBound> sch(ex, reqs, n, out, sv->slots, sv->mem_cap, sv->max_rows);
-    using clk = std::chrono::steady_clock;
-    const clk::time_point t0 = clk::now();
-    while (!sch.finished())
-        sch.step(std::chrono::duration<double>(clk::now() - t0).count());
-    if (batches) *batches = sch.batches();
+    int nb = 0;
+    const pnce_status st = guarded([&] {
+        CudaExecBound ex{CudaExec{sv, operand_elt(sv->dtype)}, reqs};
+        Scheduler<CudaExecBound> sch(ex, reqs, n, out, sv->slots, sv->mem_cap, sv->max_rows);
+        using clk = std::chrono::steady_clock;
+        const clk::time_point t0 = clk::now();
+        while (!sch.finished())
+            sch.step(std::chrono::duration<double>(clk::now() - t0).count());
+        nb = sch.batches();
+        return PNCE_OK;
+    });
+    if (batches) *batches = nb;
+    if (st != PNCE_OK) {                   // out of host memory part-way: let the GPU finish
+        for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
+        return st;
+    }
     // a kernel of these batches may have latched an error (a bounded wait that ran out, an
     // invalid descriptor): then some results may be wrong, and the run says so
     for (cudaStream_t s : sv->streams)
