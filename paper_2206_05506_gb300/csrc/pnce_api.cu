@@ -257,7 +257,12 @@ pnce_status pnce_pilot_create(pnce_handle* h, const uint32_t* bits_host, int N, 
     // wrapped table: bit t = bit (t mod N) for t < 32 * words, words = ceil(N/32) + 2, so that
     // any 32-bit window starting below N is readable from two consecutive words
     const int words = (N + 31) / 32 + 2;
-    std::vector<uint32_t> ext((size_t)words, 0u);
+    std::vector<uint32_t> ext;
+    try {
+        ext.assign((size_t)words, 0u);
+    } catch (...) {
+        return PNCE_ENOMEM;
+    }
     for (long long t = 0; t < 32LL * words; ++t) {
         const long long n = t % N;
         const uint32_t b = (bits_host[n >> 5] >> (n & 31)) & 1u;

@@ -221,7 +221,14 @@ pnce_status pnce_fmt_tables(const uint32_t* bits_host, int N, uint16_t* pos, uin
 pnce_status pnce_fmt_create(pnce_handle* h, const uint32_t* bits_host, int N, pnce_fmt** out) {
     if (!h || !bits_host || !out) return PNCE_EINVAL;
     *out = nullptr;
-    std::vector<uint16_t> pos((size_t)(N > 0 ? N : 0)), lag((size_t)(N > 0 ? N : 0));
+    if (N < 3 || (long long)N + 1 > (1LL << MAX_R)) return PNCE_EINVAL;   // before allocating
+    std::vector<uint16_t> pos, lag;
+    try {
+        pos.resize((size_t)N);
+        lag.resize((size_t)N);
+    } catch (...) {
+        return PNCE_ENOMEM;
+    }
     pnce_status st = pnce_fmt_tables(bits_host, N, pos.data(), lag.data());
     if (st != PNCE_OK) return st;
     st = on_device(h);
