@@ -413,7 +413,7 @@ class NativeServer:
     the completion event -- in C++.  Requests as for Server; run() replays them open loop
     on the calling thread and returns the same statistics."""
 
-    def __init__(self, pilot_bits, device=None, dtype: str = "fp16", slots: int = 4,
+    def __init__(self, pilot_bits, device=None, dtype: str = "fp16", slots: int = 8,
                  mem_cap_bytes: float = 40e9, max_batch_rows: int = 4096):
         self.ctx = context(device)
         self.device = self.ctx.device
