@@ -355,9 +355,11 @@ def run_serving_batch(dev, replays: int):
     cores, FP32 SIMT) and request shape: a one-stream engine replays the batch's captured
     graph (prep, gather + quantise or gather, correlation, scatter), each replay reading a
     different page-locked block from a pool larger than L2 and writing its result to
-    page-locked memory; CUDA events around each replay, median and 90th percentile."""
+    page-locked memory; CUDA events around each replay, median and 90th percentile.  Then
+    the correlation kernel alone (traced eager runs) against its roofline."""
     import torch
 
+    import paper_2206_05506_gb300 as pk
     from paper_2206_05506_gb300 import serve
     from synth import serving as S
 
@@ -384,10 +386,36 @@ def run_serving_batch(dev, replays: int):
                 e1.synchronize()
                 if i >= 20:
                     ts.append(e0.elapsed_time(e1) * 1e3)
-            out[f"{dtype}_m{M}_n{N}_kl{K * L}"] = {
-                "gpu_us_median": float(np.median(ts)),
-                "gpu_us_p90": float(np.percentile(ts, 90)), "replays": replays,
-                "bytes_in": M * N * 8, "bytes_out": M * K * L * 8}
+            # the correlation kernel's own time: eager runs of the same batch with the
+            # library's tracing on (no dependent-launch overlap, so the kernel is alone)
+            graph, shape.graph = shape.graph, None
+            pk.trace_enable(True, dev)
+            pk.trace_read(dev)
+            for i in range(20):
+                shape.run(eng, 0, [serve.Request(0, 0.0, M, N, K, L,
+                                                 pool[i % blocks].data_ptr(), H.data_ptr())])
+            torch.cuda.synchronize()
+            kind = "correlate" if dtype != "fp32" else "simt"
+            kt = [t for k, t in pk.trace_read(dev) if k == kind]
+            pk.trace_enable(False, dev)
+            shape.graph = graph
+            kern_us = float(np.median(kt)) * 1e3 if kt else None
+            flops = 4.0 * N * M * K * L                          # the request's own taps
+            peaks, _ = load_peaks()
+            row = {"gpu_us_median": float(np.median(ts)),
+                   "gpu_us_p90": float(np.percentile(ts, 90)), "replays": replays,
+                   "bytes_in": M * N * 8, "bytes_out": M * K * L * 8,
+                   "correlation_kernel_us": kern_us}
+            if kern_us:
+                achieved = flops / (kern_us * 1e-6) / 1e12
+                sms = torch.cuda.get_device_properties(dev).multi_processor_count
+                peak = (peaks["bf16_tflops"] * DTYPE_RATIO[dtype] if dtype != "fp32"
+                        else sms * 128 * 2 * 2070e6 / 1e12)
+                row["correlation_roofline"] = {
+                    "bound": "tensor" if dtype != "fp32" else "alu", "achieved": achieved,
+                    "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "note": "a lone request: a few CTAs, bound by set-up and drain latency"}
+            out[f"{dtype}_m{M}_n{N}_kl{K * L}"] = row
             del eng
         del pool
     return out
