@@ -1,9 +1,10 @@
 """Benchmark: PN-correlation channel estimation throughput on GB300.
 
 One step = one pnce_estimate call over one batch: per-antenna quantisation of the
-received blocks, then the tensor-core correlation with its epilogue, on synthetic received blocks shaped like the precision workload (M=128 antennas, N=4095
-m-sequence, K=16 transmitters x L=128 taps, 512 frames, SNR 0/10/20/30 dB), inputs
-resident in HBM.  The library's tracing records CUDA events around each kernel it
+received blocks, then the tensor-core correlation with its epilogue, on synthetic
+received blocks shaped like the precision workload (M=128 antennas, N=4095 m-sequence,
+K=16 transmitters x L=128 taps, 512 frames, SNR 0/10/20/30 dB), inputs resident in
+HBM.  The library's tracing records CUDA events around each kernel it
 launches, on the stream the kernel runs on; the correlation kernels' durations give the
 roofline figure.
 

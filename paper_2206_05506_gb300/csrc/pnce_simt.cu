@@ -8,11 +8,13 @@
 // Block tile: up to 32 antennas x 256 lags (for large grids the rows are split into
 // balanced groups so that the grid fills whole waves); thread tile: 4 antennas x 8
 // consecutive lags, so each received sample read from shared memory feeds 64 FMAs.  Grids
-// smaller than half the GPU use 1 antenna per thread (8-row blocks, 4x shorter).  Because a thread's lags
-// are consecutive, the pilot values it needs at sample n+1 are those of sample n shifted
-// by one lag: a 15-entry register window slides along the pilot, one new shared load per
-// sample.  Received samples and the pilot window of each 128-sample chunk are staged in
-// shared memory, double buffered (cp.async for Y).
+// smaller than half the GPU use 1 antenna per thread (8-row blocks, 4x shorter).  Because
+// a thread's lags are consecutive, the pilot values it needs at sample n+1 are those of
+// sample n shifted by one lag: a 15-entry register window slides along the pilot, one new
+// shared load per sample.  The pilot window of the whole reduction is staged in shared
+// memory once per block, and each warp double-buffers its own rows (cp.async); serving
+// batches use an instantiation that reads the rows from, and writes the lags into, the
+// requests' own buffers.
 #include <algorithm>
 
 #include "pnce_internal.h"
@@ -317,34 +319,33 @@ __device__ __forceinline__ void warp_rows(WSmem<RA>& sm, const float* __restrict
                 if (j < valid) hrow[j] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
             }
         }
-        return;
     } else {
-    // Serving rows go out through the warp's (now idle) staging buffer, so that a store
-    // instruction writes 256 contiguous bytes rather than 32 pieces of 8 bytes 64 bytes
-    // apart: the same for L2, but over the host link (results in page-locked memory) every
-    // partial piece would be a transfer of its own.
-    float2* sbuf = &sm.y[warp][0][0][0];             // 2 * RA * NC >= TJ entries
-    static_assert(2 * RA * NC >= TJ, "staging buffer too small for a row of results");
+        // Serving rows go out through the warp's (now idle) staging buffer, so that a store
+        // instruction writes 256 contiguous bytes rather than 32 pieces of 8 bytes 64 bytes
+        // apart: the same for L2, but over the host link (results in page-locked memory) every
+        // partial piece would be a transfer of its own.
+        float2* sbuf = &sm.y[warp][0][0][0];         // 2 * RA * NC >= TJ entries
+        static_assert(2 * RA * NC >= TJ, "staging buffer too small for a row of results");
 #pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        const long long a = a_first + i;
-        const int b = __ldg(g.row_req + a);
-        if (b < 0) continue;                         // warp-uniform: one row per iteration
-        const pnce_req_desc& q = g.dd[b];
-        const int kl = q.K * q.L;
-        float2* drow = static_cast<float2*>(q.H) + (a - q.row_offset) * kl + col0;
-        const int vrow = min(valid, kl - col0);      // lags of the tile kept for it
+        for (int i = 0; i < NR; ++i) {
+            const long long a = a_first + i;
+            const int b = __ldg(g.row_req + a);
+            if (b < 0) continue;                     // warp-uniform: one row per iteration
+            const pnce_req_desc& q = g.dd[b];
+            const int kl = q.K * q.L;
+            float2* drow = static_cast<float2*>(q.H) + (a - q.row_offset) * kl + col0;
+            const int vrow = min(valid, kl - col0);  // lags of the tile kept for it
 #pragma unroll
-        for (int r = 0; r < RJ; ++r)
-            sbuf[RJ * lane + r] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
-        __syncwarp();
+            for (int r = 0; r < RJ; ++r)
+                sbuf[RJ * lane + r] = make_float2(acc[i][r].x * invN, acc[i][r].y * invN);
+            __syncwarp();
 #pragma unroll
-        for (int k = 0; k < RJ; ++k) {
-            const int j = lane + 32 * k;
-            if (j < vrow) drow[j] = sbuf[j];
+            for (int k = 0; k < RJ; ++k) {
+                const int j = lane + 32 * k;
+                if (j < vrow) drow[j] = sbuf[j];
+            }
+            __syncwarp();                            // sbuf is rewritten for the next row
         }
-        __syncwarp();                                // sbuf is rewritten for the next row
-    }
     }
 }
 
@@ -405,8 +406,8 @@ simt_corr_warp_kernel(const uint32_t* __restrict__ bits, const float* __restrict
             warp_rows<MODE, RA, 2, GRP>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
                                    warp, lane, gio);
     } else if (nrw == 1) {
-        warp_rows<MODE, RA, 1, GRP>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H, warp,
-                               lane, gio);
+        warp_rows<MODE, RA, 1, GRP>(sm, E, Y, y_stride, a_first, N, lags, col0, valid, invN, H,
+                                    warp, lane, gio);
     }
 }
 
