@@ -441,6 +441,28 @@ __device__ __forceinline__ void few_lags_sample(const uint32_t* __restrict__ ext
         if ((wr >> j) & 1u) acc[j] = __fadd2_rn(acc[j], v);
 }
 
+// Two consecutive samples n, n + 1 (n even): their bit windows come from one 64-bit read
+// of the table (window offset q & 31 <= 31 plus K*L + 1 <= 33 bits fit in 64).
+template <int KLM>
+__device__ __forceinline__ void few_lags_pair(const uint32_t* __restrict__ ext, int N, int KL,
+                                              int n, float2 v0, float2 v1, float2& all,
+                                              float2 (&acc)[KLM]) {
+    int q = n - (KL - 1);
+    if (q < 0) q += N;
+    const uint32_t lo = __ldg(ext + (q >> 5)), hi = __ldg(ext + (q >> 5) + 1);
+    const uint64_t win = (((uint64_t)hi << 32) | lo) >> (q & 31);
+    const uint32_t wr0 = __brev((uint32_t)win) >> (32 - KL);          // sample n
+    const uint32_t wr1 = __brev((uint32_t)(win >> 1)) >> (32 - KL);   // sample n + 1
+    all = __fadd2_rn(all, v0);
+#pragma unroll
+    for (int j = 0; j < KLM; ++j)
+        if ((wr0 >> j) & 1u) acc[j] = __fadd2_rn(acc[j], v0);
+    all = __fadd2_rn(all, v1);
+#pragma unroll
+    for (int j = 0; j < KLM; ++j)
+        if ((wr1 >> j) & 1u) acc[j] = __fadd2_rn(acc[j], v1);
+}
+
 template <int KLM>
 __global__ void __launch_bounds__(256)
 simt_few_lags_kernel(const uint32_t* __restrict__ ext, const float2* __restrict__ Y,
@@ -475,12 +497,9 @@ simt_few_lags_kernel(const uint32_t* __restrict__ ext, const float2* __restrict_
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const int p = p0 + 32 * u;
-                if (p < npairs) {
-                    few_lags_sample<KLM>(ext, N, KL, 2 * p, make_float2(v[u].x, v[u].y), all,
-                                         acc);
-                    few_lags_sample<KLM>(ext, N, KL, 2 * p + 1, make_float2(v[u].z, v[u].w),
-                                         all, acc);
-                }
+                if (p < npairs)
+                    few_lags_pair<KLM>(ext, N, KL, 2 * p, make_float2(v[u].x, v[u].y),
+                                       make_float2(v[u].z, v[u].w), all, acc);
             }
         }
         // an odd last sample: the lane whose turn pair npairs would be
