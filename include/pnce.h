@@ -335,9 +335,22 @@ pnce_status pnce_estimate_grouped(pnce_handle* h, const pnce_pilot* pilot,
  *   and completion times (seconds from the start of the run), the batch index and a
  *   status (PNCE_OK, or the status that failed its batch: PNCE_ECUDA for a launch or an
  *   event error, PNCE_EINVAL for a missing pilot, PNCE_ENOMEM for a shape that could not be
- *   allocated).  Returns PNCE_EINVAL for invalid arguments (nothing run), else, after every
+ *   allocated; -1 for a request the run never got to, when it gave up part-way).  Returns PNCE_EINVAL for invalid arguments (nothing run), else, after every
  *   batch completed, the status latched on the device by the run's kernels (PNCE_OK when
  *   none; otherwise some results may be wrong).
+ * Online use (a session of requests submitted as they come, results collected as they
+ * finish; the same rules, the arrival time of a request being its submission):
+ * pnce_server_start begins a session (its clock starts at 0; PNCE_ESTATE while requests of
+ *   the previous session are still open).
+ * pnce_server_submit queues one request (req->t_arrival is ignored) and returns its ticket
+ *   (0, 1, ... in submission order); PNCE_EINVAL for an invalid request, PNCE_ESTATE with
+ *   no session.  The request's buffers must stay valid until it is reported.
+ * pnce_server_poll runs one scheduling pass (completions, admissions, launches) and
+ *   reports up to max_out finished requests -- tickets[k] with outs[k] as in
+ *   pnce_server_run -- in *n_out; the others are reported by later polls.  Results latched
+ *   on the device by the kernels are read with pnce_get_status.
+ * pnce_server_open: requests of the session not yet reported.  pnce_server_run returns
+ *   PNCE_ESTATE while any are open (the two share the slots).
  * pnce_sched_simulate: the same scheduling rules on a virtual clock, no GPU: the clock
  *   advances by clock_dt at every pass of the loop, a batch of r antennas completes
  *   base_s + per_row_s * r seconds after its launch, a request's footprint is
@@ -364,6 +377,12 @@ pnce_status pnce_server_add_pilot(pnce_server* server, const pnce_pilot* pilot);
 pnce_status pnce_server_prepare(pnce_server* server, int N, int kl_class, int capacity);
 pnce_status pnce_server_run(pnce_server* server, const pnce_serve_req* reqs, int n,
                             pnce_serve_out* out, int* batches);
+pnce_status pnce_server_start(pnce_server* server);
+pnce_status pnce_server_submit(pnce_server* server, const pnce_serve_req* req,
+                               long long* ticket);
+pnce_status pnce_server_poll(pnce_server* server, long long* tickets, pnce_serve_out* outs,
+                             int max_out, int* n_out);
+pnce_status pnce_server_open(pnce_server* server, int* n_open);
 pnce_status pnce_sched_simulate(const pnce_serve_req* reqs, int n, int slots,
                                 double mem_cap_bytes, int max_batch_rows, double row_bytes,
                                 double base_s, double per_row_s, double clock_dt,

@@ -86,6 +86,10 @@ _SIGS = {
     "pnce_server_add_pilot": (_i, [_vp, _vp]),
     "pnce_server_prepare": (_i, [_vp, _i, _i, _i]),
     "pnce_server_run": (_i, [_vp, _vp, _i, _vp, C.POINTER(_i)]),
+    "pnce_server_start": (_i, [_vp]),
+    "pnce_server_submit": (_i, [_vp, C.POINTER(ServeReq), C.POINTER(C.c_longlong)]),
+    "pnce_server_poll": (_i, [_vp, _vp, _vp, _i, C.POINTER(_i)]),
+    "pnce_server_open": (_i, [_vp, C.POINTER(_i)]),
     "pnce_sched_simulate": (_i, [_vp, _i, _i, C.c_double, _i, C.c_double, C.c_double,
                                  C.c_double, C.c_double, _i, _i, _vp, C.POINTER(_i)]),
 }

@@ -22,6 +22,7 @@
 #include <map>
 #include <memory>
 #include <tuple>
+#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -50,57 +51,75 @@ struct ReqState {
     int klc = 0;
 };
 
+// One request in the scheduler: the caller's description, what the run reports for it,
+// and its footprint and lag class.
+struct Entry {
+    pnce_serve_req r;
+    pnce_serve_out o;
+    double nbytes;
+    int klc;
+};
+
 // The scheduling rules over an executor E:
 //   double E::footprint(const pnce_serve_req&)
-//   bool   E::launch(int slot, int N, int klc, const std::vector<int>& ids, long long rows,
-//                    int* status)                      -- false: the batch failed to start
+//   bool   E::launch(int slot, int N, int klc, const std::vector<const pnce_serve_req*>& rs,
+//                    long long rows, int* status)      -- false: the batch failed to start
 //   int    E::done(int slot)                           -- 1 done, 0 running, < 0 failed
+// Requests enter with submit() (tickets 0, 1, ... in submission order), each step() polls
+// completions, admits and launches, and drain() hands over the requests finished since
+// the last drain and forgets them.
 template <class E>
 class Scheduler {
   public:
-    Scheduler(E& ex, const pnce_serve_req* reqs, int n, pnce_serve_out* out, int slots,
-              double mem_cap, int max_rows)
-        : ex_(ex), reqs_(reqs), n_(n), out_(out), cap_(mem_cap), max_rows_(max_rows) {
+    Scheduler(E& ex, int slots, double mem_cap, int max_rows)
+        : ex_(ex), cap_(mem_cap), max_rows_(max_rows) {
         for (int s = slots - 1; s >= 0; --s) free_.push_back(s);
-        st_.resize((size_t)n);
-        for (int i = 0; i < n; ++i) {
-            out_[i] = pnce_serve_out{-1.0, -1.0, -1.0, -1, 0};
-            st_[(size_t)i].klc = kl_class(reqs_[i].K * reqs_[i].L, reqs_[i].N);
-        }
     }
 
-    // one pass: submit the arrivals up to `now`, then complete, admit and launch
+    long long submit(const pnce_serve_req& r) {
+        const long long t = next_ticket_++;
+        live_.emplace(t, Entry{r, pnce_serve_out{-1.0, -1.0, -1.0, -1, 0}, ex_.footprint(r),
+                               kl_class(r.K * r.L, r.N)});
+        pending_.push_back(t);
+        return t;
+    }
+
+    // one pass: complete, admit and launch
     void step(double now) {
-        while (next_ < n_ && reqs_[next_].t_arrival <= now) {
-            st_[(size_t)next_].nbytes = ex_.footprint(reqs_[next_]);
-            pending_.push_back(next_++);
-        }
         complete(now);
         admit(now);
         launch(now);
     }
 
-    bool finished() const {
-        if (next_ < n_ || !pending_.empty() || !busy_.empty()) return false;
-        for (const auto& b : buckets_)
-            if (!b.second.empty()) return false;
-        return true;
+    // f(ticket, entry) for every request finished since the last drain
+    template <class F>
+    void drain(F&& f) {
+        for (long long t : finished_) {
+            auto it = live_.find(t);
+            f(t, it->second);
+            live_.erase(it);
+        }
+        finished_.clear();
     }
 
+    // nothing waiting, in flight or unreported
+    bool idle() const { return live_.empty(); }
     int batches() const { return batches_; }
-    double peak_inflight() const { return peak_; }
+    size_t open() const { return live_.size(); }
 
   private:
     struct Busy {
         int slot;
-        std::vector<int> ids;
+        std::vector<long long> ids;
     };
 
-    void release(const std::vector<int>& ids, double now, int status) {
-        for (int i : ids) {
-            out_[i].t_done = now;
-            out_[i].status = status;
-            inflight_ -= st_[(size_t)i].nbytes;
+    void release(const std::vector<long long>& ids, double now, int status) {
+        for (long long t : ids) {
+            Entry& e = live_.find(t)->second;
+            e.o.t_done = now;
+            e.o.status = status;
+            inflight_ -= e.nbytes;
+            finished_.push_back(t);
         }
     }
 
@@ -120,26 +139,24 @@ class Scheduler {
 
     void admit(double now) {
         while (!pending_.empty()) {
-            const int i = pending_.front();
-            const double nb = st_[(size_t)i].nbytes;
-            if (inflight_ + nb > cap_ && inflight_ > 0) break;   // wait for memory
+            Entry& e = live_.find(pending_.front())->second;
+            if (inflight_ + e.nbytes > cap_ && inflight_ > 0) break;   // wait for memory
+            inflight_ += e.nbytes;
+            e.o.t_admit = now;
+            buckets_[{e.r.N, e.klc}].push_back(pending_.front());
             pending_.pop_front();
-            inflight_ += nb;
-            peak_ = std::max(peak_, inflight_);
-            out_[i].t_admit = now;
-            buckets_[{reqs_[i].N, st_[(size_t)i].klc}].push_back(i);
         }
     }
 
     void launch(double now) {
         while (!free_.empty()) {
             // the bucket whose head arrived first; ties go to the smaller (N, klc) key
-            std::deque<int>* q = nullptr;
+            std::deque<long long>* q = nullptr;
             std::pair<int, int> key{0, 0};
             double best = 0.0;
             for (auto& b : buckets_) {
                 if (b.second.empty()) continue;
-                const double t = reqs_[b.second.front()].t_arrival;
+                const double t = live_.find(b.second.front())->second.r.t_arrival;
                 if (!q || t < best) {
                     q = &b.second;
                     key = b.first;
@@ -147,26 +164,27 @@ class Scheduler {
                 }
             }
             if (!q) return;
-            std::vector<int> ids;
+            std::vector<long long> ids;
+            std::vector<const pnce_serve_req*> rs;
             long long rows = 0;
-            while (!q->empty() && rows + reqs_[q->front()].M <= max_rows_) {
-                rows += reqs_[q->front()].M;
+            while (!q->empty()) {
+                const Entry& e = live_.find(q->front())->second;
+                if (rows + e.r.M > max_rows_ && !ids.empty()) break;
+                rows += e.r.M;                 // (a single request above max_rows goes alone)
                 ids.push_back(q->front());
+                rs.push_back(&e.r);
                 q->pop_front();
-            }
-            if (ids.empty()) {                     // a single request above max_rows
-                ids.push_back(q->front());
-                rows = reqs_[q->front()].M;
-                q->pop_front();
+                if (rows >= max_rows_) break;
             }
             const int slot = free_.back();
             free_.pop_back();
-            for (int i : ids) {
-                out_[i].t_launch = now;
-                out_[i].batch = batches_;
+            for (long long t : ids) {
+                Entry& e = live_.find(t)->second;
+                e.o.t_launch = now;
+                e.o.batch = batches_;
             }
             int status = PNCE_OK;
-            if (!ex_.launch(slot, key.first, key.second, ids, rows, &status)) {
+            if (!ex_.launch(slot, key.first, key.second, rs, rows, &status)) {
                 release(ids, now, status == PNCE_OK ? (int)PNCE_ECUDA : status);
                 free_.push_back(slot);
                 continue;
@@ -177,18 +195,16 @@ class Scheduler {
     }
 
     E& ex_;
-    const pnce_serve_req* reqs_;
-    int n_;
-    pnce_serve_out* out_;
     double cap_;
     int max_rows_;
-    std::vector<ReqState> st_;
-    int next_ = 0;
-    std::deque<int> pending_;
-    std::map<std::pair<int, int>, std::deque<int>> buckets_;
+    std::unordered_map<long long, Entry> live_;
+    std::vector<long long> finished_;
+    long long next_ticket_ = 0;
+    std::deque<long long> pending_;
+    std::map<std::pair<int, int>, std::deque<long long>> buckets_;
     std::vector<int> free_;
     std::vector<Busy> busy_;
-    double inflight_ = 0.0, peak_ = 0.0;
+    double inflight_ = 0.0;
     int batches_ = 0;
 };
 
@@ -204,7 +220,8 @@ struct SimExec {
     std::vector<char> running, fault;
     long long calls = 0, started = 0;
     double footprint(const pnce_serve_req& r) const { return (double)r.M * row_bytes; }
-    bool launch(int slot, int, int, const std::vector<int>&, long long rows, int* status) {
+    bool launch(int slot, int, int, const std::vector<const pnce_serve_req*>&, long long rows,
+                int* status) {
         ++calls;
         if (fail_launch > 0 && calls % fail_launch == 0) {
             *status = PNCE_ECUDA;
@@ -225,18 +242,35 @@ struct SimExec {
     }
 };
 
+bool req_ok(const pnce_serve_req& r) {
+    return r.M >= 1 && r.N >= 2 && r.K >= 1 && r.L >= 1 && (long long)r.K * r.L <= r.N &&
+           std::isfinite(r.t_arrival);
+}
+
 bool serve_args_ok(const pnce_serve_req* reqs, int n, const pnce_serve_out* out, int slots,
                    double mem_cap, int max_rows) {
     if (n < 0 || (n > 0 && (!reqs || !out)) || slots < 1 || slots > 64 || max_rows < 1 ||
         !(mem_cap > 0.0))
         return false;
-    for (int i = 0; i < n; ++i) {
-        const pnce_serve_req& r = reqs[i];
-        if (r.M < 1 || r.N < 2 || r.K < 1 || r.L < 1 || (long long)r.K * r.L > r.N ||
-            !std::isfinite(r.t_arrival) || (i > 0 && r.t_arrival < reqs[i - 1].t_arrival))
+    for (int i = 0; i < n; ++i)
+        if (!req_ok(reqs[i]) || (i > 0 && reqs[i].t_arrival < reqs[i - 1].t_arrival))
             return false;
-    }
     return true;
+}
+
+// Open-loop replay of a trace: at each pass the requests that have arrived by now are
+// submitted (ticket i for request i), the scheduler steps, and finished requests are
+// copied out.
+template <class S, class Clock>
+void replay(S& sch, const pnce_serve_req* reqs, int n, pnce_serve_out* out, Clock&& now_fn) {
+    for (int i = 0; i < n; ++i) out[i] = pnce_serve_out{-1.0, -1.0, -1.0, -1, -1};   // not run
+    int next = 0;
+    while (next < n || !sch.idle()) {
+        const double now = now_fn();
+        while (next < n && reqs[next].t_arrival <= now) sch.submit(reqs[next++]);
+        sch.step(now);
+        sch.drain([&](long long t, const Entry& e) { out[t] = e.o; });
+    }
 }
 
 // The entry points allocate through the standard library; nothing may throw across the C
@@ -266,11 +300,8 @@ extern "C" pnce_status pnce_sched_simulate(const pnce_serve_req* reqs, int n, in
         SimExec ex{&t, base_s, per_row_s, row_bytes, fail_launch_every, fail_done_every,
                    std::vector<double>((size_t)slots, 0.0), std::vector<char>((size_t)slots, 0),
                    std::vector<char>((size_t)slots, 0)};
-        Scheduler<SimExec> sch(ex, reqs, n, out, slots, mem_cap, max_batch_rows);
-        while (!sch.finished()) {
-            t += clock_dt;
-            sch.step(t);
-        }
+        Scheduler<SimExec> sch(ex, slots, mem_cap, max_batch_rows);
+        replay(sch, reqs, n, out, [&] { return t += clock_dt; });
         if (batches) *batches = sch.batches();
         return PNCE_OK;
     });
@@ -301,6 +332,8 @@ struct pnce_server {
     std::vector<cudaEvent_t> events;
     std::map<int, const pnce_pilot*> pilots;                 // by N; not owned
     std::map<std::tuple<int, int, int, int>, std::unique_ptr<ServeShape>> shapes;
+    void* online = nullptr;                                  // OnlineSession, owned
+    void (*online_free)(void*) = nullptr;
 };
 
 namespace {
@@ -381,8 +414,8 @@ struct CudaExec {
         const double pitch = (double)((r.N + 63) / 64 * 64);
         return (double)r.M * (8.0 * r.N + 2.0 * elt * pitch + 8.0 * kl_class(r.K * r.L, r.N));
     }
-    bool launch(int slot, int N, int klc, const std::vector<int>& ids, long long rows,
-                int* status, const pnce_serve_req* reqs) {
+    bool launch(int slot, int N, int klc, const std::vector<const pnce_serve_req*>& rs,
+                long long rows, int* status) {
         ServeShape* sh = nullptr;
         const pnce_status st = get_shape(sv, slot, N, klc, capacity_for(rows), &sh);
         if (st != PNCE_OK) {
@@ -390,9 +423,9 @@ struct CudaExec {
             return false;
         }
         int off = 0;
-        const int n = (int)ids.size();
+        const int n = (int)rs.size();
         for (int k = 0; k < n; ++k) {
-            const pnce_serve_req& r = reqs[ids[(size_t)k]];
+            const pnce_serve_req& r = *rs[(size_t)k];
             sh->desc[k] = pnce_req_desc{r.Y, r.H, r.M, r.K, r.L, off};
             off += r.M;
         }
@@ -416,17 +449,22 @@ struct CudaExec {
     }
 };
 
-// binds the request table to CudaExec's launch (the scheduler passes ids only)
-struct CudaExecBound {
+// An online session: requests submitted one by one and stamped with the session clock,
+// each poll one scheduling pass; finished requests wait in `ready` until reported.
+struct OnlineSession {
     CudaExec ex;
-    const pnce_serve_req* reqs;
-    double footprint(const pnce_serve_req& r) const { return ex.footprint(r); }
-    bool launch(int slot, int N, int klc, const std::vector<int>& ids, long long rows,
-                int* status) {
-        return ex.launch(slot, N, klc, ids, rows, status, reqs);
+    Scheduler<CudaExec> sch;
+    std::chrono::steady_clock::time_point t0;
+    std::deque<std::pair<long long, pnce_serve_out>> ready;
+    OnlineSession(pnce_server* sv, int elt)
+        : ex{sv, elt}, sch(ex, sv->slots, sv->mem_cap, sv->max_rows),
+          t0(std::chrono::steady_clock::now()) {}
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     }
-    int done(int slot) { return ex.done(slot); }
 };
+void online_free(void* p) { delete static_cast<OnlineSession*>(p); }
+OnlineSession* online_of(pnce_server* sv) { return static_cast<OnlineSession*>(sv->online); }
 
 int operand_elt(int dtype) {
     switch (dtype) {
@@ -481,6 +519,7 @@ pnce_status pnce_server_create(pnce_handle* h, int dtype, int slots, double mem_
 pnce_status pnce_server_destroy(pnce_server* sv) {
     if (!sv) return PNCE_EINVAL;
     for (cudaStream_t s : sv->streams) cudaStreamSynchronize(s);
+    if (sv->online) sv->online_free(sv->online);
     for (auto& kv : sv->shapes) free_shape(kv.second.get());
     for (cudaEvent_t e : sv->events) cudaEventDestroy(e);
     for (cudaStream_t s : sv->streams) cudaStreamDestroy(s);
@@ -530,17 +569,20 @@ pnce_status pnce_server_run(pnce_server* sv, const pnce_serve_req* reqs, int n,
         return PNCE_EINVAL;
     for (int i = 0; i < n; ++i)
         if (!reqs[i].Y || !reqs[i].H) return PNCE_EINVAL;
+    // the online session's batches use the same slots and tables
+    const OnlineSession* o = online_of(sv);
+    if (o && (!o->sch.idle() || !o->ready.empty())) return PNCE_ESTATE;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return PNCE_ECUDA;
     if (dev != sv->h->device) return PNCE_ESTATE;
     int nb = 0;
     const pnce_status st = guarded([&] {
-        CudaExecBound ex{CudaExec{sv, operand_elt(sv->dtype)}, reqs};
-        Scheduler<CudaExecBound> sch(ex, reqs, n, out, sv->slots, sv->mem_cap, sv->max_rows);
+        CudaExec ex{sv, operand_elt(sv->dtype)};
+        Scheduler<CudaExec> sch(ex, sv->slots, sv->mem_cap, sv->max_rows);
         using clk = std::chrono::steady_clock;
         const clk::time_point t0 = clk::now();
-        while (!sch.finished())
-            sch.step(std::chrono::duration<double>(clk::now() - t0).count());
+        replay(sch, reqs, n, out,
+               [&] { return std::chrono::duration<double>(clk::now() - t0).count(); });
         nb = sch.batches();
         return PNCE_OK;
     });
@@ -554,6 +596,63 @@ pnce_status pnce_server_run(pnce_server* sv, const pnce_serve_req* reqs, int n,
     for (cudaStream_t s : sv->streams)
         if (cudaStreamSynchronize(s) != cudaSuccess) return PNCE_ECUDA;
     return pnce_get_status(sv->h, sv->streams[0]);
+}
+
+pnce_status pnce_server_start(pnce_server* sv) {
+    if (!sv) return PNCE_EINVAL;
+    OnlineSession* o = online_of(sv);
+    if (o && (!o->sch.idle() || !o->ready.empty())) return PNCE_ESTATE;   // still open
+    return guarded([&] {
+        auto fresh = std::make_unique<OnlineSession>(sv, operand_elt(sv->dtype));
+        if (sv->online) sv->online_free(sv->online);
+        sv->online = fresh.release();
+        sv->online_free = online_free;
+        return PNCE_OK;
+    });
+}
+
+pnce_status pnce_server_submit(pnce_server* sv, const pnce_serve_req* req, long long* ticket) {
+    if (!sv || !req || !ticket) return PNCE_EINVAL;
+    OnlineSession* o = online_of(sv);
+    if (!o) return PNCE_ESTATE;
+    pnce_serve_req r = *req;
+    r.t_arrival = o->now();
+    if (!r.Y || !r.H || !req_ok(r)) return PNCE_EINVAL;
+    return guarded([&] {
+        *ticket = o->sch.submit(r);
+        return PNCE_OK;
+    });
+}
+
+pnce_status pnce_server_poll(pnce_server* sv, long long* tickets, pnce_serve_out* outs,
+                             int max_out, int* n_out) {
+    if (!sv || !n_out || max_out < 0 || (max_out > 0 && (!tickets || !outs))) return PNCE_EINVAL;
+    *n_out = 0;
+    OnlineSession* o = online_of(sv);
+    if (!o) return PNCE_ESTATE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return PNCE_ECUDA;
+    if (dev != sv->h->device) return PNCE_ESTATE;
+    return guarded([&] {
+        o->sch.step(o->now());
+        o->sch.drain([&](long long t, const Entry& e) { o->ready.emplace_back(t, e.o); });
+        int k = 0;
+        while (k < max_out && !o->ready.empty()) {
+            tickets[k] = o->ready.front().first;
+            outs[k] = o->ready.front().second;
+            o->ready.pop_front();
+            ++k;
+        }
+        *n_out = k;
+        return PNCE_OK;
+    });
+}
+
+pnce_status pnce_server_open(pnce_server* sv, int* n) {
+    if (!sv || !n) return PNCE_EINVAL;
+    OnlineSession* o = online_of(sv);
+    *n = o ? (int)(o->sch.open() + o->ready.size()) : 0;
+    return PNCE_OK;
 }
 
 }  // extern "C"

@@ -449,16 +449,49 @@ class NativeServer:
         for N in {r.N for r in requests}:
             self.pilot(N)
         reqs = _req_table(requests)
-        out = np.empty(len(requests), dtype=OUT_DTYPE)
+        out = np.zeros(len(requests), dtype=OUT_DTYPE)
+        out["batch"] = -1
+        out["status"] = -1                              # not run (the call fills it in)
         nb = C.c_int(0)
         with torch.cuda.device(self.device):
             st = lib().pnce_server_run(self._s, reqs.ctypes.data, len(requests),
-                                            out.ctypes.data, C.byref(nb))
-        if st == _lib.PNCE_EINVAL:
-            check(st, "pnce_server_run")
+                                       out.ctypes.data, C.byref(nb))
+        if st != _lib.PNCE_OK and np.all(out["status"] == -1):
+            check(st, "pnce_server_run")                # refused before running anything
         stats = _native_stats(requests, out, nb.value)
         check(st, "pnce_server_run")                   # a status latched on the device
         return stats
+
+    # -- online use: requests submitted as they come, results collected as they finish
+    def start(self):
+        """Begin a session (its clock starts now)."""
+        check(lib().pnce_server_start(self._s), "pnce_server_start")
+
+    def submit(self, r: Request) -> int:
+        """Queue one request (arriving now); returns its ticket.  Its buffers must stay
+        valid until poll() reports it."""
+        self.pilot(r.N)
+        q = _lib.ServeReq(r.y_addr, r.h_addr, r.M, r.N, r.K, r.L, 0.0)
+        t = C.c_longlong(0)
+        check(lib().pnce_server_submit(self._s, C.byref(q), C.byref(t)), "pnce_server_submit")
+        return t.value
+
+    def poll(self, max_out: int = 256) -> list:
+        """One scheduling pass; [(ticket, result)] of up to max_out finished requests, each
+        result an OUT_DTYPE record (times from the session start, batch, status)."""
+        tickets = np.empty(max(1, max_out), dtype=np.int64)
+        outs = np.empty(max(1, max_out), dtype=OUT_DTYPE)
+        n = C.c_int(0)
+        with torch.cuda.device(self.device):
+            check(lib().pnce_server_poll(self._s, tickets.ctypes.data, outs.ctypes.data,
+                                         max_out, C.byref(n)), "pnce_server_poll")
+        return [(int(tickets[k]), outs[k]) for k in range(n.value)]
+
+    def open_requests(self) -> int:
+        """Requests of the session not yet reported by poll()."""
+        n = C.c_int(0)
+        check(lib().pnce_server_open(self._s, C.byref(n)), "pnce_server_open")
+        return n.value
 
     def __del__(self):
         s = getattr(self, "_s", None)

@@ -137,3 +137,45 @@ def test_native_pilot_replacement_recaptures(setup):
         ref = O.estimate(pool[(r.M, r.N)][[specs[reqs.index(r)].slot]], S.pilot_bits(r.N),
                          r.K, r.L)
         assert O.nmse(_result(out, r)[None], ref) <= TOL["fp16"]
+
+
+def test_native_online_session(setup):
+    # requests submitted one by one while earlier ones run, results collected by polling:
+    # every ticket reported once, each result the oracle's, and a trace run refused while
+    # the session has open requests
+    from paper_2206_05506_gb300 import PnceError
+    serve, pool, pinned = setup
+    dev = torch.device("cuda", 0)
+    specs = S.poisson_trace(20000.0, 0.004, seed=25, payload_slots=2)
+    total = sum(s.M * s.K * s.L for s in specs)
+    out = torch.zeros(total, dtype=torch.complex64, pin_memory=True)
+    nat = serve.NativeServer(S.pilot_bits, device=dev, dtype="fp16", slots=3)
+    nat.prepare(sorted({s.N for s in specs}), caps=(64, 256))
+    reqs = _requests(serve, pinned, specs, out)
+    nat.start()
+    seen = {}
+    tickets = []
+    for k, r in enumerate(reqs):
+        tickets.append(nat.submit(r))
+        if k == 0:
+            with pytest.raises(PnceError):            # the session shares the slots
+                nat.run([r])
+            with pytest.raises(PnceError):            # the session is still open
+                nat.start()
+        for t, o in nat.poll(max_out=4):
+            seen[t] = o
+    assert tickets == list(range(len(reqs)))
+    for _ in range(100000):
+        if nat.open_requests() == 0:
+            break
+        for t, o in nat.poll(max_out=4):
+            assert t not in seen
+            seen[t] = o
+    assert nat.open_requests() == 0 and sorted(seen) == tickets
+    for t, r in zip(tickets, reqs):
+        o = seen[t]
+        assert o["status"] == 0 and 0 <= o["t_admit"] <= o["t_launch"] < o["t_done"]
+        ref = O.estimate(pool[(r.M, r.N)][[specs[t].slot]], S.pilot_bits(r.N), r.K, r.L)
+        assert O.nmse(_result(out, r)[None], ref) <= TOL["fp16"]
+    nat.start()                                       # a new session once all are reported
+    assert nat.open_requests() == 0
