@@ -45,3 +45,20 @@ def test_clock_summary_keeps_the_window_and_reads_reasons():
     assert s["power_w_median"] == 410.0
     assert s["reasons"] == ["sw_power_cap"]
     assert bench.ClockSampler.summarize(lines, 5.0, 6.0) is None
+
+
+def test_nmse_stats_by_hand():
+    # four frames of two entries, SNR labels 0, 10, 0, 10; frame f has reference energy 2
+    # and error energy e_f, so its NMSE is e_f / 2, and each SNR pools its frames
+    import numpy as np
+    ref = np.ones((4, 2), dtype=np.complex64)
+    est = ref.copy()
+    est[0, 0] += 1.0          # e = 1
+    est[1, 1] += 2.0j         # e = 4
+    est[2, 0] += 0.5          # e = 0.25
+    st = bench.nmse_stats(est, ref, [0, 10, 0, 10], chunk=3)   # a chunk boundary inside
+    assert st["frames"] == 4
+    assert abs(st["nmse"] - (1 + 4 + 0.25) / 8) < 1e-12
+    assert abs(st["nmse_by_snr_db"]["0"] - (1 + 0.25) / 4) < 1e-12
+    assert abs(st["nmse_by_snr_db"]["10"] - 4 / 4) < 1e-12
+    assert abs(st["nmse_worst_frame"] - 2.0) < 1e-12
