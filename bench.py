@@ -239,6 +239,20 @@ SWEEP_RATES_HZ = (10000.0, 20000.0, 40000.0, 80000.0, 120000.0, 160000.0)
 SERVING_STREAMS = 8
 
 
+def knee_of(sweep: list):
+    """The highest offered rate (rows in increasing order) still delivered (>= 95 %) with
+    p99 within 4x of the lowest rate's, or None."""
+    if not sweep:
+        return None
+    base_p99 = sweep[0]["p99_ms"]
+    knee = None
+    for row in sweep:
+        if row["delivered_frames_per_s"] >= 0.95 * row["offered_hz"] and \
+                row["p99_ms"] <= 4.0 * base_p99:
+            knee = row["offered_hz"]
+    return knee
+
+
 def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
                 sweep_rates=SWEEP_RATES_HZ, sweep_seconds: float = 2.0):
     """Poisson request stream (uneven M, N, K, L) through the continuous-batching server,
@@ -320,14 +334,8 @@ def run_serving(dev, seconds: float, rate_hz: float = 20000.0, refs=None,
                           "p50_ms": sst["p50_ms"], "p99_ms": sst["p99_ms"],
                           "max_ms": sst["max_ms"], "mean_batch_rows": sst["mean_batch_rows"],
                           "failed": sst["failed"]})
-        base_p99 = sweep[0]["p99_ms"] if sweep else None
-        knee = None
-        for row in sweep:
-            if row["delivered_frames_per_s"] >= 0.95 * row["offered_hz"] and \
-                    row["p99_ms"] <= 4.0 * base_p99:
-                knee = row["offered_hz"]
         st["rate_sweep"] = {"seconds_per_rate": sweep_seconds, "rows": sweep,
-                            "knee_offered_hz": knee}
+                            "knee_offered_hz": knee_of(sweep)}
         return st
 
     res["loop"] = ("native: the scheduling loop in the library (pnce_server_run); "

@@ -62,3 +62,16 @@ def test_nmse_stats_by_hand():
     assert abs(st["nmse_by_snr_db"]["0"] - (1 + 0.25) / 4) < 1e-12
     assert abs(st["nmse_by_snr_db"]["10"] - 4 / 4) < 1e-12
     assert abs(st["nmse_worst_frame"] - 2.0) < 1e-12
+
+
+def test_serving_knee_rule():
+    def row(rate, delivered, p99):
+        return {"offered_hz": rate, "delivered_frames_per_s": delivered, "p99_ms": p99}
+    sweep = [row(10e3, 9.97e3, 0.06), row(20e3, 19.9e3, 0.065), row(40e3, 39.8e3, 0.24),
+             row(80e3, 79.8e3, 0.241), row(160e3, 146e3, 170.0)]
+    assert bench.knee_of(sweep) == 40e3          # 80k: p99 just above 4x the 10k one
+    sweep[3]["p99_ms"] = 0.24
+    assert bench.knee_of(sweep) == 80e3
+    sweep[3]["delivered_frames_per_s"] = 0.94 * 80e3   # not delivered
+    assert bench.knee_of(sweep) == 40e3
+    assert bench.knee_of([]) is None
