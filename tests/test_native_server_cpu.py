@@ -75,3 +75,25 @@ def test_simulated_faults_match_python_loop():
     np.testing.assert_array_equal(out["t_done"], [r.t_done for r in py])
     np.testing.assert_array_equal(out["t_launch"], [r.t_launch for r in py])
     assert nb == srv.batches
+
+
+def test_native_stats_by_hand():
+    # three requests: two in batch 0, one in batch 1, one of them failed; latencies 1 ms
+    # and 3 ms for the two that finished
+    from paper_2206_05506_gb300 import serve
+    reqs = [Request(0, 0.000, 64, 255, 1, 16, 0, 0), Request(1, 0.001, 32, 255, 2, 16, 0, 0),
+            Request(2, 0.002, 128, 511, 1, 64, 0, 0)]
+    out = np.zeros(3, dtype=serve.OUT_DTYPE)
+    out["t_admit"] = [0.0, 0.001, 0.002]
+    out["t_launch"] = [0.0005, 0.0015, 0.0025]
+    out["t_done"] = [0.001, 0.004, 0.003]
+    out["batch"] = [0, 0, 1]
+    out["status"] = [0, 0, 4]
+    st = serve._native_stats(reqs, out, 2)
+    assert st["requests"] == 2 and st["failed"] == 1 and st["batches"] == 2
+    assert abs(st["mean_batch_rows"] - (96 + 128) / 2) < 1e-12
+    assert abs(st["max_ms"] - 3.0) < 1e-9 and abs(st["p50_ms"] - 2.0) < 1e-9
+    assert abs(st["frames_per_s"] - 2 / 0.004) < 1e-6
+    assert abs(st["taps_per_s"] - (64 * 16 + 32 * 32) / 0.004) < 1e-3
+    assert reqs[2].error == "status 4" and reqs[0].error == "" and reqs[1].batch == 0
+    assert reqs[1].t_done == 0.004
