@@ -77,6 +77,37 @@ def test_null_arguments_rejected_without_device(lib):
                              None) == 1
 
 
+def test_serving_loop_rejects_bad_arguments_without_device(lib):
+    # the native serving loop's entry points validate before any CUDA call
+    import ctypes as C
+    from paper_2206_05506_gb300 import _lib
+    out = C.c_void_p()
+    n = C.c_int(0)
+    t = C.c_longlong(0)
+    req = _lib.ServeReq(None, None, 4, 7, 1, 1, 0.0)
+    assert lib.pnce_server_create(None, 2, 4, 1e9, 4096, C.byref(out)) == 1
+    assert lib.pnce_server_destroy(None) == 1
+    assert lib.pnce_server_add_pilot(None, None) == 1
+    assert lib.pnce_server_prepare(None, 7, 4, 64) == 1
+    assert lib.pnce_server_run(None, None, 0, None, C.byref(n)) == 1
+    assert lib.pnce_server_start(None) == 1
+    assert lib.pnce_server_submit(None, C.byref(req), C.byref(t)) == 1
+    assert lib.pnce_server_poll(None, None, None, 0, C.byref(n)) == 1
+    assert lib.pnce_server_open(None, C.byref(n)) == 1
+    outs = (_lib.ServeOut * 1)()
+    bad = (_lib.ServeReq * 1)(_lib.ServeReq(None, None, 4, 7, 8, 1, 0.0))   # K*L > N
+    assert lib.pnce_sched_simulate(bad, 1, 2, 1e9, 4096, 1000.0, 2e-4, 2e-7, 5e-6, 0, 0,
+                                   outs, C.byref(n)) == 1
+    ok = (_lib.ServeReq * 1)(_lib.ServeReq(None, None, 4, 7, 1, 1, 0.0))
+    assert lib.pnce_sched_simulate(ok, 1, 0, 1e9, 4096, 1000.0, 2e-4, 2e-7, 5e-6, 0, 0,
+                                   outs, C.byref(n)) == 1                 # no slot
+    assert lib.pnce_sched_simulate(ok, 1, 2, 1e9, 4096, 1000.0, 2e-4, 2e-7, 5e-6, -1, 0,
+                                   outs, C.byref(n)) == 1                 # bad fault period
+    assert lib.pnce_sched_simulate(ok, 1, 2, 1e9, 4096, 1000.0, 2e-4, 2e-7, 5e-6, 0, 0,
+                                   outs, C.byref(n)) == 0 and n.value == 1
+    assert outs[0].status == 0 and outs[0].t_done > outs[0].t_launch >= 0.0
+
+
 def test_missing_library_fails_loudly():
     # no CPU or PyTorch fallback: without the built library the binding refuses to run
     from paper_2206_05506_gb300 import _lib
